@@ -1,0 +1,360 @@
+"""Benchmark of the FX correlator hot path on one GB300 (or N replicas).
+
+One step = F-engine (FFT + int8 re-packing + corner turn) + X-engine (INT8,
+exact) + integration dump to FP64, over one integration of the INT8 workload:
+256 antennas x 2 pol = 512 inputs, 1024 channels, 4096 spectra (4.29 GB of raw
+complex int8 voltages per step, larger than L2, so no flush is needed).
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (n_ant, n_pol, n_chan, n_spectra)
+    "B": (256, 2, 1024, 4096),
+    "small": (64, 2, 256, 1024),
+}
+METRIC = "X-engine complex-MAC/s and % tensor peak; F-engine GB/s; vs FP32 baseline at tol"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sus=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), src="measured")
+    return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(n_ant, n_pol, N, K, seed=0, n_chan_sample=2, spectra_sample=None):
+    """Time the FP64 oracle on a bounded sample of the workload: the direct DFT of
+    `n_chan_sample` channels for every input over `spectra_sample` spectra, their
+    int8 re-packing, and the triple-loop CMAC of those channels. Returns
+    (cMAC/s, seconds, cores, description)."""
+    import oracle
+    import synth
+
+    Ks = K if spectra_sample is None else spectra_sample
+    v = synth.volt_int8(n_ant, n_pol, N, Ks, seed=seed)
+    n_in = n_ant * n_pol
+    bins = np.arange(n_chan_sample) * (N // n_chan_sample) + 3
+    scale = np.full(N, 1.0 / np.sqrt(N), np.float32)
+    oracle.build()
+    t0 = time.perf_counter()
+    S = oracle.channelise(v, N, bins)
+    q, _ = oracle.requant(S, scale[bins])
+    oracle.cmac(q)
+    dt = time.perf_counter() - t0
+    cmacs = n_chan_sample * (n_in * (n_in + 1) // 2) * Ks
+    cores = len(os.sched_getaffinity(0))
+    desc = (f"oracle DFT+requant+CMAC of {n_chan_sample} of {N} channels, all {n_in} inputs, "
+            f"{Ks} of {K} spectra")
+    return cmacs / dt, dt, cores, desc
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    n_ant, n_pol, N, K = WORKLOADS[args.workload]
+    n_in = n_ant * n_pol
+    Ks = max(64, K // 16)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps are not repeated
+    rates, secs = [], []
+    for s in range(args.steps):
+        r, dt, cores, desc = cpu_oracle_sample(n_ant, n_pol, N, K, seed=s, n_chan_sample=1, spectra_sample=Ks)
+        rates.append(r)
+        secs.append(dt)
+    v = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "cMAC/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _workload_name(args.workload)},
+        "cpu_baseline": {"value": v, "unit": "cMAC/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "cMAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _workload_name(w):
+    n_ant, n_pol, N, K = WORKLOADS[w]
+    return (f"INT8 FX: {n_ant} antennas x {n_pol} pol = {n_ant * n_pol} inputs, {N}-point FFT / {N} channels, "
+            f"{K} spectra per integration, complex int8 voltages sigma=16 + delayed point source")
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1305_5639_gb300 import build as pbuild
+
+    pbuild.build()
+    from paper_1305_5639_gb300 import api
+    import synth
+
+    n_ant, n_pol, N, K = WORKLOADS[args.workload]
+    n_in = n_ant * n_pol
+    B = n_in * (n_in + 1) // 2
+    cmac_step = N * B * K
+
+    volt_h = synth.volt_int8(n_ant, n_pol, N, K, seed=rank)
+    volt_pin = torch.from_numpy(volt_h).pin_memory()
+    del volt_h
+    volt = volt_pin.to(dev, non_blocking=False)
+    corr = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine=args.xengine)
+    chan = corr.chan_buffer()
+    # requantisation scale from a calibration pass: 16 / per-component RMS of each channel
+    power = corr.fengine_power(volt)
+    scale = (16.0 / torch.sqrt(power)).contiguous()
+    stream = torch.cuda.current_stream()
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        corr.fengine(volt, scale, chan)
+        if evs:
+            evs[1].record(stream)
+        corr.xengine(chan)
+        if evs:
+            evs[2].record(stream)
+        corr.dump(copy=False)
+        if evs:
+            evs[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    corr.check_status()
+    torch.cuda.synchronize()
+
+    evs = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    clk = ClockSampler(dev.index)
+    clk.start()
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = ev()
+    t1 = ev()
+    t0.record(stream)
+    for s in range(args.steps):
+        step(evs[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    corr.check_status()
+    ms = t0.elapsed_time(t1)
+    f_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    x_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    d_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ws * cmac_step / (ms_step * 1e-3)
+
+    # ---- end to end: pinned host voltages in, FP64 visibilities out, every step
+    vis_pin = torch.empty((N, B), dtype=torch.complex128).pin_memory()
+    vis_dev = torch.empty((N, B), dtype=torch.complex128, device=dev)
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        volt.copy_(volt_pin, non_blocking=True)
+        corr.fengine(volt, scale, chan)
+        corr.xengine(chan)
+        corr.dump(vis_dev)
+        vis_pin.copy_(vis_dev, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / e2e_steps
+    corr.reset()
+
+    # ---- CUDA-core comparator at the same accuracy (exact dp4a INT8 X-engine), same data
+    cc_ms = None
+    if args.comparator:
+        cc = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine="cudacore")
+        cc.xengine(chan)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        cc.xengine(chan)
+        b.record(stream)
+        torch.cuda.synchronize()
+        cc_ms = a.elapsed_time(b)
+        cc.close()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peaks = _peaks()
+    x_flops = 8.0 * cmac_step
+    f_bytes = 2.0 * n_in * N * K * 2  # read + write complex int8
+    tensor = corr_uses_tc(args.xengine)
+    x_ach = x_flops / (x_ms * 1e-3) / 1e12
+    if tensor:
+        roof = {"bound": "tensor", "achieved": x_ach, "peak": peaks["bf16_sus"], "unit": "TFLOP/s",
+                "frac": x_ach / peaks["bf16_sus"], "traffic": None,
+                "kernel": "X-engine INT8-exact (tcgen05 kind::f16)",
+                "peak_note": f"{peaks['src']} sustained bf16 dense (fp16 runs at the same rate)"}
+    else:
+        roof = {"bound": "alu", "achieved": x_ach, "peak": None, "unit": "TOP/s", "frac": None,
+                "traffic": None, "kernel": "X-engine INT8 CUDA-core dp4a"}
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        r, dt, cores, desc = cpu_oracle_sample(n_ant, n_pol, N, K, n_chan_sample=1, spectra_sample=max(64, K // 16))
+        cpu = {"value": r, "unit": "cMAC/s", "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
+    launches = 3 + (1 if True else 0)  # F-engine, X-engine, dump (+ power pass outside the timed region)
+    line = {
+        "metric": METRIC, "value": value, "unit": "cMAC/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": _workload_name(args.workload), "l2": "inputs larger than L2 (4.29 GB per step)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "stages_ms": {"fengine": f_ms, "xengine": x_ms, "dump": d_ms},
+        "xengine_cmac_per_s": cmac_step / (x_ms * 1e-3),
+        "fengine_gbs": f_bytes / (f_ms * 1e-3) / 1e9,
+        "fengine_hbm_frac": f_bytes / (f_ms * 1e-3) / 1e9 / peaks["hbm"],
+        "dump_gbs": (N * B * (8 + 32)) / (d_ms * 1e-3) / 1e9,
+        "cudacore_comparator": None if cc_ms is None else {
+            "xengine_ms": cc_ms, "cmac_per_s": cmac_step / (cc_ms * 1e-3), "speedup_tensor_vs_cudacore": cc_ms / x_ms,
+            "accuracy": "both exact (bit-identical INT32)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * cmac_step / (e2e_ms * 1e-3), "unit": "cMAC/s",
+                "h2d_bytes_per_step": int(volt.numel()), "d2h_bytes_per_step": int(vis_pin.numel() * 16),
+                "ms_per_step": e2e_ms},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    corr.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def corr_uses_tc(xengine: str) -> bool:
+    return xengine in ("auto", "tcgen05")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="B", choices=sorted(WORKLOADS))
+    ap.add_argument("--xengine", default="auto", choices=["auto", "cudacore", "tcgen05"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    ap.add_argument("--comparator", type=int, default=1, help="time the CUDA-core X-engine once")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

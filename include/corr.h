@@ -1,0 +1,166 @@
+/*
+ * corr.h -- C ABI of libcorr, a single-GPU (sm_103a) FX correlator.
+ *
+ * The library computes the data-parallel hot path of the FX correlator described
+ * in Wang & Harris (2013), Section 2:
+ *   F-engine (Eq. 1): per input, per spectrum a, S_a,i[k] = sum_{n<N} s_i[aN+n] e^{-j 2 pi k n / N},
+ *                     unnormalised, bins 0..N-1 in natural order, no window;
+ *   X-engine (Eq. 2): per channel k, V_ij[k] = sum_a S_a,i[k] conj(S_a,j[k]) for all
+ *                     i >= j (autocorrelations included: the "triangle" of Section 4).
+ * The library emits V_ij = conj(C_ij) of Eq. 2 (the conjugate sits on the second
+ * index); magnitudes and autocorrelations are identical.
+ *
+ * Conventions for every entry point:
+ *   - n_in = n_ant * n_pol inputs; input index i = ant * n_pol + pol.
+ *   - B = n_in (n_in + 1) / 2 packed visibilities per channel, packed index
+ *     b(i, j) = i (i + 1) / 2 + j for i >= j.
+ *   - Complex values are interleaved (re, im): complex int8 = 2 x int8,
+ *     complex float = float2, complex double = double2.
+ *   - All data pointers are DEVICE pointers owned by the caller unless stated; the
+ *     library owns the integration accumulator, the FP64 long-integration buffer,
+ *     twiddle tables and status words, and frees them in corr_destroy.
+ *   - All calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream) and return a status code; they never abort the process.
+ *     Argument errors are reported before anything is enqueued.
+ *   - A handle is not thread-safe: calls on one handle must be serialised by the
+ *     caller (they may use different streams if the caller orders them).
+ */
+#ifndef CORR_H
+#define CORR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CORR_API __attribute__((visibility("default")))
+#else
+#define CORR_API
+#endif
+
+typedef struct corr_s corr_t;
+typedef int32_t corr_status;
+
+enum {
+    CORR_OK = 0,
+    CORR_EINVAL = 1,       /* bad argument (null, size, alignment, precision mismatch) */
+    CORR_ENOMEM = 2,       /* device allocation failed */
+    CORR_ECUDA = 3,        /* a CUDA runtime call failed; see corr_last_error() */
+    CORR_EOVERFLOW = 4,    /* INT32 integration accumulator could overflow */
+    CORR_ESTATE = 5,       /* call not valid in the handle's current state */
+    CORR_ETIMEOUT = 6,     /* a bounded device-side wait gave up (kernel returned early) */
+    CORR_EUNSUPPORTED = 7  /* shape or mode not supported by this build */
+};
+
+/* Arithmetic of the X-engine. */
+enum {
+    CORR_PREC_FP32 = 0,      /* float input, FP32 CUDA-core FFMA */
+    CORR_PREC_INT8 = 1,      /* complex int8 input, exact integer result (INT32) */
+    CORR_PREC_FP16 = 2,      /* float input rounded to FP16, FP32 accumulation (tensor cores) */
+    CORR_PREC_FP16_HILO = 3  /* float input split x = h + 2^-11 l into two FP16 parts,
+                                V ~ hh + 2^-11 (hl + lh), FP32 accumulation (tensor cores) */
+};
+
+/* X-engine implementation. AUTO picks tcgen05 tensor cores for INT8/FP16/FP16_HILO
+ * and CUDA cores for FP32. CUDACORE with INT8 uses exact dp4a integer arithmetic. */
+enum { CORR_XENG_AUTO = 0, CORR_XENG_CUDACORE = 1, CORR_XENG_TCGEN05 = 2 };
+
+typedef struct corr_opts {
+    int32_t precision; /* CORR_PREC_*, default CORR_PREC_FP32 */
+    int32_t xengine;   /* CORR_XENG_*, default CORR_XENG_AUTO */
+    int32_t flags;     /* reserved, must be 0 */
+    int32_t device;    /* CUDA device ordinal; -1 = the current device */
+} corr_opts;
+
+/* Create a correlator for n_ant x n_pol inputs, an n_chan-point FFT (n_chan
+ * channels) and n_spectra spectra per integration (Section 2: A spectra per
+ * accumulation). opts may be NULL (FP32, AUTO, current device).
+ * The F-engine supports n_chan in {16, 64, 256, 1024}; the X-engine any
+ * n_chan >= 1. For INT8, n_spectra * 2 * 127^2 must stay below 2^31
+ * (CORR_EOVERFLOW otherwise). *out receives the handle (NULL on error). */
+CORR_API corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_spectra,
+                        const corr_opts *opts, corr_t **out);
+
+/* Free every library-owned buffer. Synchronises the device. NULL is accepted. */
+CORR_API corr_status corr_destroy(corr_t *h);
+
+/* Static string for a status code. */
+CORR_API const char *corr_status_str(corr_status s);
+
+/* Text of the last CUDA error seen on this thread ("" if none). */
+CORR_API const char *corr_last_error(void);
+
+/* Number of packed visibilities per channel, n_in (n_in + 1) / 2. */
+CORR_API int64_t corr_n_baselines(const corr_t *h);
+
+/* F-engine, Eq. 1 (Section 2), for one integration.
+ *   volt      [n_in][n_spectra * n_chan] complex time series; spectrum a of input i
+ *             is samples a*n_chan .. a*n_chan + n_chan - 1. Complex int8 for
+ *             CORR_PREC_INT8 (the paper's 8-bit streams, Section 5), complex float
+ *             otherwise. 16-byte aligned.
+ *   chan_scale [n_chan] float, INT8 only (must be NULL otherwise): per-channel
+ *             re-quantisation scale. Each of Re, Im of S * scale_k is clamped to
+ *             [-127, 127] and rounded half-to-even to int8 (8-bit packing of the
+ *             expanded spectra, Section 6.2).
+ *   chan_out  [n_chan][n_in][n_spectra] channel-major ("corner-turned") output:
+ *             complex int8 for INT8, complex float (FP32 FFT, unnormalised)
+ *             otherwise. 16-byte aligned. */
+CORR_API corr_status corr_fengine(corr_t *h, const void *volt, const float *chan_scale, void *chan_out,
+                         void *stream);
+
+/* Per-channel mean power per real component of the F-engine spectra,
+ * power[k] = sum_{i,a} |S_a,i[k]|^2 / (2 n_in n_spectra), in FP32 (atomics; not
+ * bit-reproducible). Used to set chan_scale = target_rms / sqrt(power).
+ *   volt as for corr_fengine; power [n_chan] float (device), overwritten. */
+CORR_API corr_status corr_fengine_power(corr_t *h, const void *volt, float *power, void *stream);
+
+/* X-engine, Eq. 2 (Section 2), for one integration of n_spectra spectra: adds
+ * V'_ij[k] = g_i conj(g_j) sum_a X_a,i[k] conj(X_a,j[k]) (i >= j) into the
+ * library-owned integration accumulator.
+ *   chan_in [n_chan][n_in][n_spectra]: complex int8 for INT8, complex float
+ *           otherwise (FP16 paths round or split it on the fly). 16-byte aligned.
+ *   gains   [n_in] complex float, or NULL for unit gains. Not allowed with INT8
+ *           (the INT8 result is an exact integer; CORR_EINVAL).
+ * INT8: accumulator is INT32 per component; CORR_EOVERFLOW if the spectra
+ * accumulated since the last dump would exceed the INT32 guard. */
+CORR_API corr_status corr_xengine(corr_t *h, const void *chan_in, const float *gains, void *stream);
+
+/* Copy the current integration accumulator to out: [n_chan][B] complex int32
+ * (2 x int32) for INT8, complex float otherwise. Device pointer. */
+CORR_API corr_status corr_get_accum(corr_t *h, void *out, void *stream);
+
+/* Integration dump: vis64 += accumulator (FP64), accumulator = 0. If vis_out is
+ * not NULL, the FP64 long-integration buffer is copied to it
+ * ([n_chan][B] complex double, device). Asynchronous. */
+CORR_API corr_status corr_dump(corr_t *h, double *vis_out, void *stream);
+
+/* Read and clear the handle's device status word. Returns CORR_ETIMEOUT (or
+ * another CORR_* code) if a kernel of this handle gave up early since the last
+ * check, CORR_OK otherwise. Synchronises `stream`. */
+CORR_API corr_status corr_check_status(corr_t *h, void *stream);
+
+/* Zero the accumulator and the FP64 long-integration buffer. */
+CORR_API corr_status corr_reset(corr_t *h, void *stream);
+
+/* Adjoint of corr_xengine (with gains) for gradient-based gain calibration.
+ *   grad_vis  [n_chan][B] complex float: G_ij = dL/dV'_ij (PyTorch convention
+ *             dL/dRe + j dL/dIm) of the gained visibilities, packed i >= j.
+ *   chan_in   [n_chan][n_in][n_spectra] complex float: the forward input X.
+ *   gains     [n_in] complex float, or NULL for unit gains.
+ *   grad_chan [n_chan][n_in][n_spectra] complex float or NULL:
+ *             dL/dX_f = diag(conj g) G^_f diag(g) X_f,
+ *   grad_gains [n_in] complex float or NULL:
+ *             dL/dg_m = sum_f sum_j G^_f,mj g_j V_f,jm,
+ * with G^ the Hermitian completion of G (G^_ij = G_ij for i > j,
+ * G^_ji = conj G_ij, G^_ii = 2 Re G_ii). FP32 precision only (CORR_ESTATE
+ * otherwise). */
+CORR_API corr_status corr_backward(corr_t *h, const float *grad_vis, const void *chan_in, const float *gains,
+                          float *grad_chan, float *grad_gains, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORR_H */

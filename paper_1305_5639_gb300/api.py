@@ -1,0 +1,165 @@
+"""Thin Python binding of the libcorr C ABI (include/corr.h), same names.
+
+Only argument marshalling happens here: tensors are passed as raw device pointers
+and the CUDA stream defaults to torch's current stream. Every step of the
+correlator runs in the library's kernels.
+
+Tensor conventions (all on the handle's CUDA device, contiguous):
+  complex int8   -> torch.int8 with a trailing dimension of 2 (re, im)
+  complex float  -> torch.complex64, or torch.float32 with a trailing 2
+  complex double -> torch.complex128, or torch.float64 with a trailing 2
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import PREC, XENG, CorrError, check, corr_opts  # noqa: F401
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not t.is_cuda:
+        raise ValueError("libcorr takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("libcorr takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def corr_create(n_ant: int, n_pol: int, n_chan: int, n_spectra: int, precision="fp32", xengine="auto",
+                device: int = -1) -> ctypes.c_void_p:
+    lib = _lib.load()
+    o = corr_opts(PREC[precision] if isinstance(precision, str) else int(precision),
+                  XENG[xengine] if isinstance(xengine, str) else int(xengine), 0, int(device))
+    h = ctypes.c_void_p()
+    check(lib.corr_create(n_ant, n_pol, n_chan, n_spectra, ctypes.byref(o), ctypes.byref(h)), "corr_create")
+    return h
+
+
+def corr_destroy(h) -> None:
+    check(_lib.load().corr_destroy(h), "corr_destroy")
+
+
+def corr_n_baselines(h) -> int:
+    return int(_lib.load().corr_n_baselines(h))
+
+
+def corr_fengine(h, volt, chan_scale, chan_out, stream=None) -> None:
+    check(_lib.load().corr_fengine(h, _ptr(volt), _ptr(chan_scale), _ptr(chan_out), _stream(stream)),
+          "corr_fengine")
+
+
+def corr_fengine_power(h, volt, power, stream=None) -> None:
+    check(_lib.load().corr_fengine_power(h, _ptr(volt), _ptr(power), _stream(stream)), "corr_fengine_power")
+
+
+def corr_xengine(h, chan_in, gains=None, stream=None) -> None:
+    check(_lib.load().corr_xengine(h, _ptr(chan_in), _ptr(gains), _stream(stream)), "corr_xengine")
+
+
+def corr_get_accum(h, out, stream=None) -> None:
+    check(_lib.load().corr_get_accum(h, _ptr(out), _stream(stream)), "corr_get_accum")
+
+
+def corr_dump(h, vis_out=None, stream=None) -> None:
+    check(_lib.load().corr_dump(h, _ptr(vis_out), _stream(stream)), "corr_dump")
+
+
+def corr_check_status(h, stream=None) -> None:
+    check(_lib.load().corr_check_status(h, _stream(stream)), "corr_check_status")
+
+
+def corr_reset(h, stream=None) -> None:
+    check(_lib.load().corr_reset(h, _stream(stream)), "corr_reset")
+
+
+def corr_backward(h, grad_vis, chan_in, gains=None, grad_chan=None, grad_gains=None, stream=None) -> None:
+    check(_lib.load().corr_backward(h, _ptr(grad_vis), _ptr(chan_in), _ptr(gains), _ptr(grad_chan),
+                                    _ptr(grad_gains), _stream(stream)), "corr_backward")
+
+
+class Correlator:
+    """Owns one libcorr handle; allocates outputs as torch tensors."""
+
+    def __init__(self, n_ant: int, n_pol: int, n_chan: int, n_spectra: int, precision="fp32", xengine="auto",
+                 device=None):
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else int(device))
+        self.device = dev
+        self.n_ant, self.n_pol, self.n_chan, self.n_spectra = n_ant, n_pol, n_chan, n_spectra
+        self.n_in = n_ant * n_pol
+        self.precision = precision
+        with torch.cuda.device(dev):
+            self.h = corr_create(n_ant, n_pol, n_chan, n_spectra, precision, xengine, dev.index)
+        self.n_base = corr_n_baselines(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            corr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- buffers
+    def chan_buffer(self):
+        if self.precision == "int8":
+            return torch.empty((self.n_chan, self.n_in, self.n_spectra, 2), dtype=torch.int8, device=self.device)
+        return torch.empty((self.n_chan, self.n_in, self.n_spectra), dtype=torch.complex64, device=self.device)
+
+    def accum_buffer(self):
+        if self.precision == "int8":
+            return torch.empty((self.n_chan, self.n_base, 2), dtype=torch.int32, device=self.device)
+        return torch.empty((self.n_chan, self.n_base), dtype=torch.complex64, device=self.device)
+
+    # -- calls
+    def fengine(self, volt, chan_scale=None, out=None, stream=None):
+        out = self.chan_buffer() if out is None else out
+        corr_fengine(self.h, volt, chan_scale, out, stream)
+        return out
+
+    def fengine_power(self, volt, out=None, stream=None):
+        out = torch.empty(self.n_chan, dtype=torch.float32, device=self.device) if out is None else out
+        corr_fengine_power(self.h, volt, out, stream)
+        return out
+
+    def xengine(self, chan_in, gains=None, stream=None):
+        corr_xengine(self.h, chan_in, gains, stream)
+
+    def accum(self, out=None, stream=None):
+        out = self.accum_buffer() if out is None else out
+        corr_get_accum(self.h, out, stream)
+        return out
+
+    def dump(self, out=None, stream=None, copy=True):
+        if copy and out is None:
+            out = torch.empty((self.n_chan, self.n_base), dtype=torch.complex128, device=self.device)
+        corr_dump(self.h, out if copy else None, stream)
+        return out
+
+    def check_status(self, stream=None):
+        corr_check_status(self.h, stream)
+
+    def reset(self, stream=None):
+        corr_reset(self.h, stream)
+
+    def backward(self, grad_vis, chan_in, gains=None, want_chan=True, want_gains=True, stream=None):
+        gc = torch.empty_like(chan_in) if want_chan else None
+        gg = torch.empty(self.n_in, dtype=torch.complex64, device=self.device) if want_gains else None
+        corr_backward(self.h, grad_vis, chan_in, gains, gc, gg, stream)
+        return gc, gg

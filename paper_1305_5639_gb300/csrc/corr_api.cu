@@ -1,0 +1,312 @@
+// Host side of the libcorr C ABI: argument checking, handle state, buffer
+// ownership and kernel dispatch. Every entry point returns a status code.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+namespace corr {
+
+static thread_local char g_last_error[512] = "";
+
+void set_cuda_error(cudaError_t e, const char *what) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+}
+
+corr_status check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_cuda_error(e, what);
+        return CORR_ECUDA;
+    }
+    return CORR_OK;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+void free_buffers(Handle &h) {
+    cudaFree(h.acc);
+    cudaFree(h.vis64);
+    cudaFree(h.twiddle);
+    cudaFree(h.status);
+    cudaFree(h.power64);
+    cudaFree(h.bwd_ws);
+    h.acc = nullptr;
+    h.vis64 = nullptr;
+    h.twiddle = nullptr;
+    h.status = nullptr;
+    h.power64 = nullptr;
+    h.bwd_ws = nullptr;
+}
+
+bool use_tc(const Handle &h) {
+    if (h.xengine == CORR_XENG_CUDACORE) return false;
+    if (h.xengine == CORR_XENG_TCGEN05) return true;
+    return h.precision != CORR_PREC_FP32;
+}
+
+}  // namespace
+}  // namespace corr
+
+using corr::Handle;
+
+struct corr_s {
+    Handle h;
+};
+
+extern "C" {
+
+const char *corr_status_str(corr_status s) {
+    switch (s) {
+        case CORR_OK: return "CORR_OK";
+        case CORR_EINVAL: return "CORR_EINVAL: invalid argument";
+        case CORR_ENOMEM: return "CORR_ENOMEM: device allocation failed";
+        case CORR_ECUDA: return "CORR_ECUDA: CUDA runtime error";
+        case CORR_EOVERFLOW: return "CORR_EOVERFLOW: INT32 accumulator could overflow";
+        case CORR_ESTATE: return "CORR_ESTATE: invalid call in the current state";
+        case CORR_ETIMEOUT: return "CORR_ETIMEOUT: a device-side wait timed out";
+        case CORR_EUNSUPPORTED: return "CORR_EUNSUPPORTED: unsupported shape or mode";
+        default: return "CORR_?: unknown status";
+    }
+}
+
+const char *corr_last_error(void) { return corr::g_last_error; }
+
+int64_t corr_n_baselines(const corr_t *h) { return h ? h->h.n_base : -1; }
+
+corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_spectra, const corr_opts *opts,
+                        corr_t **out) {
+    if (!out) return CORR_EINVAL;
+    *out = nullptr;
+    if (n_ant <= 0 || n_pol <= 0 || n_chan <= 0 || n_spectra <= 0) return CORR_EINVAL;
+    const int64_t n_in = (int64_t)n_ant * n_pol;
+    if (n_in > (1 << 16)) return CORR_EINVAL;
+    corr_opts o{CORR_PREC_FP32, CORR_XENG_AUTO, 0, -1};
+    if (opts) o = *opts;
+    if (o.precision < CORR_PREC_FP32 || o.precision > CORR_PREC_FP16_HILO) return CORR_EINVAL;
+    if (o.xengine < CORR_XENG_AUTO || o.xengine > CORR_XENG_TCGEN05) return CORR_EINVAL;
+    if (o.flags != 0) return CORR_EINVAL;
+    if (o.precision == CORR_PREC_INT8) {
+        // INT32 guard: |Re V| <= n_spectra * 2 * 127^2 must stay below 2^31
+        if ((int64_t)n_spectra * 2 * 127 * 127 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
+    }
+    if ((o.precision == CORR_PREC_FP16 || o.precision == CORR_PREC_FP16_HILO) && o.xengine == CORR_XENG_CUDACORE)
+        return CORR_EUNSUPPORTED;
+
+    corr_s *c = new (std::nothrow) corr_s();
+    if (!c) return CORR_ENOMEM;
+    Handle &h = c->h;
+    h.n_ant = n_ant;
+    h.n_pol = n_pol;
+    h.n_in = (int32_t)n_in;
+    h.n_chan = n_chan;
+    h.n_spectra = n_spectra;
+    h.n_base = n_in * (n_in + 1) / 2;
+    h.precision = o.precision;
+    h.xengine = o.xengine;
+    if (o.device >= 0) {
+        h.device = o.device;
+    } else if (cudaGetDevice(&h.device) != cudaSuccess) {
+        corr::set_cuda_error(cudaGetLastError(), "cudaGetDevice");
+        delete c;
+        return CORR_ECUDA;
+    }
+    corr::DeviceGuard dg(h.device);
+    if (!dg.ok) {
+        corr::set_cuda_error(cudaGetLastError(), "cudaSetDevice");
+        delete c;
+        return CORR_ECUDA;
+    }
+    if (cudaDeviceGetAttribute(&h.n_sm, cudaDevAttrMultiProcessorCount, h.device) != cudaSuccess) {
+        corr::set_cuda_error(cudaGetLastError(), "cudaDeviceGetAttribute");
+        delete c;
+        return CORR_ECUDA;
+    }
+    const size_t nvis = (size_t)h.n_chan * (size_t)h.n_base;
+    const size_t acc_bytes = nvis * 8;  // int2 or float2
+    bool ok = cudaMalloc(&h.acc, acc_bytes) == cudaSuccess && cudaMalloc(&h.vis64, nvis * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&h.status, sizeof(int32_t)) == cudaSuccess &&
+              cudaMalloc(&h.power64, sizeof(double) * (size_t)n_chan) == cudaSuccess;
+    if (ok && corr::fengine_supported(n_chan)) ok = cudaMalloc(&h.twiddle, sizeof(float2) * (size_t)n_chan) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        corr::free_buffers(h);
+        delete c;
+        return CORR_ENOMEM;
+    }
+    ok = cudaMemset(h.acc, 0, acc_bytes) == cudaSuccess && cudaMemset(h.vis64, 0, nvis * sizeof(double2)) == cudaSuccess &&
+         cudaMemset(h.status, 0, sizeof(int32_t)) == cudaSuccess;
+    if (ok && h.twiddle) {
+        // W_N^m = exp(-j 2 pi m / N) in double, rounded once to float
+        std::vector<float2> tw((size_t)n_chan);
+        for (int m = 0; m < n_chan; ++m) {
+            double ang = 2.0 * M_PI * (double)m / (double)n_chan;
+            tw[(size_t)m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+        }
+        ok = cudaMemcpy(h.twiddle, tw.data(), sizeof(float2) * (size_t)n_chan, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) {
+        corr::set_cuda_error(cudaGetLastError(), "corr_create init");
+        corr::free_buffers(h);
+        delete c;
+        return CORR_ECUDA;
+    }
+    *out = c;
+    return CORR_OK;
+}
+
+corr_status corr_destroy(corr_t *c) {
+    if (!c) return CORR_OK;
+    corr::DeviceGuard dg(c->h.device);
+    cudaDeviceSynchronize();
+    corr::free_buffers(c->h);
+    delete c;
+    return CORR_OK;
+}
+
+corr_status corr_fengine(corr_t *c, const void *volt, const float *chan_scale, void *chan_out, void *stream) {
+    if (!c || !volt || !chan_out) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (!corr::fengine_supported(h.n_chan)) return CORR_EUNSUPPORTED;
+    if (!corr::aligned16(volt) || !corr::aligned16(chan_out)) return CORR_EINVAL;
+    if (h.precision == CORR_PREC_INT8) {
+        if (!chan_scale) return CORR_EINVAL;
+    } else if (chan_scale) {
+        return CORR_EINVAL;
+    }
+    corr::DeviceGuard dg(h.device);
+    return corr::launch_fengine(h, volt, chan_scale, chan_out, corr::as_stream(stream));
+}
+
+corr_status corr_fengine_power(corr_t *c, const void *volt, float *power, void *stream) {
+    if (!c || !volt || !power) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (!corr::fengine_supported(h.n_chan)) return CORR_EUNSUPPORTED;
+    if (!corr::aligned16(volt)) return CORR_EINVAL;
+    corr::DeviceGuard dg(h.device);
+    return corr::launch_fengine_power(h, volt, power, corr::as_stream(stream));
+}
+
+corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, void *stream) {
+    if (!c || !chan_in) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (!corr::aligned16(chan_in)) return CORR_EINVAL;
+    if (gains && h.precision == CORR_PREC_INT8) return CORR_EINVAL;
+    if (h.precision == CORR_PREC_INT8) {
+        if ((h.acc_spectra + h.n_spectra) * 2 * 127 * 127 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
+    }
+    corr::DeviceGuard dg(h.device);
+    const bool store = h.acc_zero;
+    const float2 *g = reinterpret_cast<const float2 *>(gains);
+    corr_status s = corr::use_tc(h) ? corr::launch_xengine_tc(h, chan_in, g, store, corr::as_stream(stream))
+                                    : corr::launch_xengine_cudacore(h, chan_in, g, store, corr::as_stream(stream));
+    if (s == CORR_OK) {
+        h.acc_zero = false;
+        h.acc_spectra += h.n_spectra;
+    }
+    return s;
+}
+
+corr_status corr_get_accum(corr_t *c, void *out, void *stream) {
+    if (!c || !out) return CORR_EINVAL;
+    Handle &h = c->h;
+    corr::DeviceGuard dg(h.device);
+    CORR_CUDA_TRY(cudaMemcpyAsync(out, h.acc, (size_t)h.n_chan * h.n_base * 8, cudaMemcpyDeviceToDevice,
+                                  corr::as_stream(stream)));
+    return CORR_OK;
+}
+
+corr_status corr_dump(corr_t *c, double *vis_out, void *stream) {
+    if (!c) return CORR_EINVAL;
+    Handle &h = c->h;
+    corr::DeviceGuard dg(h.device);
+    cudaStream_t st = corr::as_stream(stream);
+    if (!h.acc_zero) {
+        corr_status s = corr::launch_dump(h, st);
+        if (s != CORR_OK) return s;
+        h.acc_zero = true;
+        h.acc_spectra = 0;
+    }
+    if (vis_out) {
+        CORR_CUDA_TRY(cudaMemcpyAsync(vis_out, h.vis64, (size_t)h.n_chan * h.n_base * sizeof(double2),
+                                      cudaMemcpyDeviceToDevice, st));
+    }
+    return CORR_OK;
+}
+
+corr_status corr_check_status(corr_t *c, void *stream) {
+    if (!c) return CORR_EINVAL;
+    Handle &h = c->h;
+    corr::DeviceGuard dg(h.device);
+    int32_t v = 0;
+    cudaStream_t st = corr::as_stream(stream);
+    CORR_CUDA_TRY(cudaMemcpyAsync(&v, h.status, sizeof(v), cudaMemcpyDeviceToHost, st));
+    CORR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (v != 0) {
+        CORR_CUDA_TRY(cudaMemsetAsync(h.status, 0, sizeof(int32_t), st));
+        return (corr_status)v;
+    }
+    return CORR_OK;
+}
+
+corr_status corr_reset(corr_t *c, void *stream) {
+    if (!c) return CORR_EINVAL;
+    Handle &h = c->h;
+    corr::DeviceGuard dg(h.device);
+    cudaStream_t st = corr::as_stream(stream);
+    const size_t nvis = (size_t)h.n_chan * h.n_base;
+    CORR_CUDA_TRY(cudaMemsetAsync(h.acc, 0, nvis * 8, st));
+    CORR_CUDA_TRY(cudaMemsetAsync(h.vis64, 0, nvis * sizeof(double2), st));
+    h.acc_zero = true;
+    h.acc_spectra = 0;
+    return CORR_OK;
+}
+
+corr_status corr_backward(corr_t *c, const float *grad_vis, const void *chan_in, const float *gains, float *grad_chan,
+                          float *grad_gains, void *stream) {
+    if (!c || !grad_vis || !chan_in) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (h.precision != CORR_PREC_FP32) return CORR_ESTATE;
+    if (!grad_chan && !grad_gains) return CORR_OK;
+    if (!corr::aligned16(chan_in) || (grad_chan && !corr::aligned16(grad_chan))) return CORR_EINVAL;
+    corr::DeviceGuard dg(h.device);
+    if (grad_gains) {
+        const size_t need = corr::backward_workspace_bytes(h);
+        if (h.bwd_ws_bytes < need) {
+            cudaFree(h.bwd_ws);
+            h.bwd_ws = nullptr;
+            h.bwd_ws_bytes = 0;
+            if (cudaMalloc(&h.bwd_ws, need) != cudaSuccess) {
+                cudaGetLastError();
+                return CORR_ENOMEM;
+            }
+            h.bwd_ws_bytes = need;
+        }
+    }
+    return corr::launch_backward_ws(h, reinterpret_cast<const float2 *>(grad_vis),
+                                    static_cast<const float2 *>(chan_in), reinterpret_cast<const float2 *>(gains),
+                                    reinterpret_cast<float2 *>(grad_chan), reinterpret_cast<float2 *>(grad_gains),
+                                    h.bwd_ws, corr::as_stream(stream));
+}
+
+}  // extern "C"

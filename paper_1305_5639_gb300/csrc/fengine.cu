@@ -1,0 +1,231 @@
+// F-engine: per-input channelisation by an unnormalised forward DFT (Eq. 1,
+// Section 2), 8-bit re-packing of the spectra and corner turn to channel-major
+// order, in one pass.
+//
+// Each N = T x T point FFT is computed by T threads in two register passes
+// (four-step / Cooley-Tukey split n = t + T m, k = k1 + T k2):
+//   pass 1: thread t holds x[t + T m], m < T, and computes the T-point DFT over m;
+//           the result is multiplied by W_N^(t k1) (twiddle table in shared memory)
+//   exchange through shared memory (padded rows, conflict-free)
+//   pass 2: thread k1 holds Y[t][k1], t < T, and computes the T-point DFT over t,
+//           giving X[k1 + T k2].
+// A CTA handles one input and SB consecutive spectra; the outputs are staged in
+// shared memory as [channel][spectrum] so that every (channel, input) row segment
+// of SB spectra is written to global memory contiguously (the corner turn).
+#include "fft_common.cuh"
+#include "internal.h"
+
+namespace corr {
+namespace {
+
+constexpr int kThreads = 256;
+
+constexpr int isqrt_pow4(int n) { return n <= 1 ? 1 : 2 * isqrt_pow4(n / 4); }
+
+enum Mode { kFloatOut = 0, kRequant = 1, kPower = 2 };
+
+template <int N, bool I8, int MODE>
+struct FCfg {
+    static constexpr int T = isqrt_pow4(N);
+    static_assert(T * T == N, "N must be a power of 4");
+    static constexpr int G = kThreads / T;  // FFTs in flight per CTA
+    static constexpr int EXS = T + 1;       // exchange row stride (float2)
+    // spectra per CTA
+    static constexpr int SB = MODE == kRequant ? 16 : (MODE == kFloatOut ? 8 : 16);
+    static_assert(SB % (G < SB ? G : SB) == 0 || G >= SB, "");
+    // staging row stride in 32-bit words
+    static constexpr int ROWW = MODE == kRequant ? SB / 2 + 1 : (MODE == kFloatOut ? 2 * SB + 2 : 0);
+    static constexpr size_t tw_bytes = sizeof(float2) * N;
+    static constexpr size_t ex_bytes = sizeof(float2) * (size_t)G * T * EXS;
+    static constexpr size_t sc_bytes = sizeof(float) * N;
+    static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW;
+    static constexpr size_t smem = tw_bytes + ex_bytes + sc_bytes + st_bytes;
+};
+
+__device__ __forceinline__ uint32_t pack_q(float2 v, float sc) {
+    // Re-pack to int8: clamp(S * scale) to [-127, 127], round half to even.
+    float re = fminf(fmaxf(v.x * sc, -127.0f), 127.0f);
+    float im = fminf(fmaxf(v.y * sc, -127.0f), 127.0f);
+    int qr = __float2int_rn(re);
+    int qi = __float2int_rn(im);
+    return (uint32_t)(qr & 0xff) | ((uint32_t)(qi & 0xff) << 8);
+}
+
+template <int N, bool I8, int MODE>
+__global__ void __launch_bounds__(kThreads) k_fengine(const void *__restrict__ volt,
+                                                      const float *__restrict__ scale,
+                                                      void *__restrict__ out,
+                                                      double *__restrict__ power, int n_in, int K,
+                                                      const float2 *__restrict__ tw_glob) {
+    using C = FCfg<N, I8, MODE>;
+    constexpr int T = C::T, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *twid = reinterpret_cast<float2 *>(smem_raw);                        // [T k1][T t]
+    float2 *ex = reinterpret_cast<float2 *>(smem_raw + C::tw_bytes);            // [G][T][EXS]
+    float *scs = reinterpret_cast<float *>(smem_raw + C::tw_bytes + C::ex_bytes);  // [N]
+    uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::tw_bytes + C::ex_bytes + C::sc_bytes);
+
+    const int i = blockIdx.y;
+    const int a0 = blockIdx.x * SB;
+    for (int m = threadIdx.x; m < N; m += kThreads) {
+        int k1 = m / T, t = m % T;
+        twid[m] = tw_glob[(t * k1) % N];
+        if constexpr (MODE == kRequant) scs[m] = scale[m];
+        if constexpr (MODE == kPower) scs[m] = 0.0f;
+    }
+    __syncthreads();
+
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x % T;
+    float2 *exg = ex + (size_t)g * T * EXS;
+    float pw[T];
+    if constexpr (MODE == kPower) {
+#pragma unroll
+        for (int q = 0; q < T; ++q) pw[q] = 0.0f;
+    }
+
+    for (int s0 = 0; s0 < SB; s0 += G) {
+        const int s = s0 + g;
+        const int a = a0 + s;
+        const bool valid = (s < SB) && (a < K);
+        float2 v[T];
+        // ---- pass 1: thread t takes x[t + T m]
+        const size_t base = ((size_t)i * K + (size_t)(valid ? a : 0)) * N + t;
+        if constexpr (I8) {
+            const char2 *src = reinterpret_cast<const char2 *>(volt) + base;
+#pragma unroll
+            for (int m = 0; m < T; ++m) {
+                char2 c = valid ? __ldg(src + (size_t)T * m) : make_char2(0, 0);
+                v[m] = make_float2((float)c.x, (float)c.y);
+            }
+        } else {
+            const float2 *src = reinterpret_cast<const float2 *>(volt) + base;
+#pragma unroll
+            for (int m = 0; m < T; ++m) v[m] = valid ? __ldg(src + (size_t)T * m) : make_float2(0.f, 0.f);
+        }
+        fft_dif<T>(v);  // v[bitrev(k1)] = Y[t][k1]
+        sfor<0, T>([&](auto K1) {
+            constexpr int k1 = decltype(K1)::value;
+            float2 y = v[bitrev(k1, ilog2(T))];
+            if constexpr (k1 != 0) y = cmul(y, twid[k1 * T + t]);
+            exg[k1 * EXS + t] = y;
+        });
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+        // ---- pass 2: thread t now plays k1 = t and takes Y[tt][k1]
+#pragma unroll
+        for (int tt = 0; tt < T; ++tt) v[tt] = exg[t * EXS + tt];
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+        fft_dif<T>(v);  // v[bitrev(k2)] = X[t + T k2]
+        if (valid) {
+            sfor<0, T>([&](auto K2) {
+                constexpr int k2 = decltype(K2)::value;
+                const int k = t + T * k2;
+                float2 x = v[bitrev(k2, ilog2(T))];
+                if constexpr (MODE == kRequant) {
+                    uint32_t q = pack_q(x, scs[k]);
+                    reinterpret_cast<uint16_t *>(stg)[(size_t)k * (2 * ROWW) + s] = (uint16_t)q;
+                } else if constexpr (MODE == kFloatOut) {
+                    reinterpret_cast<float2 *>(stg)[(size_t)k * (ROWW / 2) + s] = x;
+                } else {
+                    pw[k2] += x.x * x.x + x.y * x.y;
+                }
+            });
+        }
+    }
+
+    if constexpr (MODE == kPower) {
+        sfor<0, T>([&](auto K2) {
+            constexpr int k2 = decltype(K2)::value;
+            atomicAdd(&scs[t + T * k2], pw[k2]);
+        });
+        __syncthreads();
+        for (int m = threadIdx.x; m < N; m += kThreads) atomicAdd(&power[m], (double)scs[m]);
+        return;
+    } else {
+        __syncthreads();
+        // ---- corner turn: row (k, i) gets spectra a0 .. a0 + nv - 1
+        const int nv = min(SB, K - a0);
+        if constexpr (MODE == kRequant) {
+            uint16_t *dst = reinterpret_cast<uint16_t *>(out);
+            const uint16_t *sh = reinterpret_cast<const uint16_t *>(stg);
+            if (nv == SB && (K % 2) == 0) {
+                constexpr int WPR = SB / 2;  // words per row
+                for (int w = threadIdx.x; w < N * WPR; w += kThreads) {
+                    int k = w / WPR, c = w % WPR;
+                    uint32_t val = stg[(size_t)k * ROWW + c];
+                    uint32_t *d = reinterpret_cast<uint32_t *>(dst + ((size_t)k * n_in + i) * K + a0);
+                    d[c] = val;
+                }
+            } else {
+                for (int e = threadIdx.x; e < N * SB; e += kThreads) {
+                    int k = e / SB, c = e % SB;
+                    if (c < nv) dst[((size_t)k * n_in + i) * K + a0 + c] = sh[(size_t)k * (2 * ROWW) + c];
+                }
+            }
+        } else {
+            float2 *dst = reinterpret_cast<float2 *>(out);
+            const float2 *sh = reinterpret_cast<const float2 *>(stg);
+            for (int e = threadIdx.x; e < N * SB; e += kThreads) {
+                int k = e / SB, c = e % SB;
+                if (c < nv) dst[((size_t)k * n_in + i) * K + a0 + c] = sh[(size_t)k * (ROWW / 2) + c];
+            }
+        }
+    }
+}
+
+template <int N, bool I8, int MODE>
+corr_status launch_one(const Handle &h, const void *volt, const float *scale, void *out, double *power,
+                       cudaStream_t st) {
+    using C = FCfg<N, I8, MODE>;
+    auto kern = k_fengine<N, I8, MODE>;
+    CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+    dim3 grid((h.n_spectra + C::SB - 1) / C::SB, h.n_in);
+    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, h.n_in, h.n_spectra, h.twiddle);
+    return check_launch("k_fengine");
+}
+
+template <int MODE>
+corr_status dispatch(const Handle &h, const void *volt, const float *scale, void *out, double *power,
+                     cudaStream_t st) {
+    const bool i8 = h.precision == CORR_PREC_INT8;
+#define CORR_F_CASE(NN)                                                                  \
+    case NN:                                                                             \
+        return i8 ? launch_one<NN, true, MODE>(h, volt, scale, out, power, st)           \
+                  : launch_one<NN, false, MODE>(h, volt, scale, out, power, st);
+    switch (h.n_chan) {
+        CORR_F_CASE(16)
+        CORR_F_CASE(64)
+        CORR_F_CASE(256)
+        CORR_F_CASE(1024)
+        default: return CORR_EUNSUPPORTED;
+    }
+#undef CORR_F_CASE
+}
+
+}  // namespace
+
+bool fengine_supported(int n) { return n == 16 || n == 64 || n == 256 || n == 1024; }
+
+corr_status launch_fengine(const Handle &h, const void *volt, const float *scale, void *out,
+                           cudaStream_t st) {
+    if (h.precision == CORR_PREC_INT8) return dispatch<kRequant>(h, volt, scale, out, nullptr, st);
+    return dispatch<kFloatOut>(h, volt, nullptr, out, nullptr, st);
+}
+
+namespace {
+__global__ void k_power_finalize(const double *__restrict__ p64, float *__restrict__ out, int n, double inv) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = (float)(p64[k] * inv);
+}
+}  // namespace
+
+corr_status launch_fengine_power(const Handle &h, const void *volt, float *power, cudaStream_t st) {
+    CORR_CUDA_TRY(cudaMemsetAsync(h.power64, 0, sizeof(double) * h.n_chan, st));
+    corr_status s = dispatch<kPower>(h, volt, nullptr, nullptr, h.power64, st);
+    if (s != CORR_OK) return s;
+    const double inv = 1.0 / (2.0 * (double)h.n_in * (double)h.n_spectra);
+    k_power_finalize<<<(h.n_chan + 255) / 256, 256, 0, st>>>(h.power64, power, h.n_chan, inv);
+    return check_launch("k_power_finalize");
+}
+
+}  // namespace corr

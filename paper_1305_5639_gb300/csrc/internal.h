@@ -1,0 +1,61 @@
+// Internal declarations shared by the libcorr translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "corr.h"
+
+namespace corr {
+
+// Handle state. Device buffers are owned by the library.
+struct Handle {
+    int32_t n_ant, n_pol, n_in, n_chan, n_spectra;
+    int64_t n_base;  // B = n_in (n_in + 1) / 2
+    int32_t precision, xengine;
+    int32_t device;
+    int32_t n_sm;
+    // integration accumulator [n_chan][B]: int2 (INT8) or float2 (float paths)
+    void *acc = nullptr;
+    bool acc_zero = true;        // accumulator known to be all-zero (X-engine may store instead of add)
+    int64_t acc_spectra = 0;     // spectra accumulated since the last dump (INT8 overflow guard)
+    double2 *vis64 = nullptr;    // FP64 long-integration buffer [n_chan][B]
+    float2 *twiddle = nullptr;   // W_N^m = exp(-j 2 pi m / N), m in [0, N)
+    int32_t *status = nullptr;   // device status word (0 ok, else CORR_* code set by a kernel)
+    double *power64 = nullptr;   // [n_chan] scratch for corr_fengine_power
+    float2 *bwd_ws = nullptr;    // dg partials for corr_backward (allocated on first use)
+    size_t bwd_ws_bytes = 0;
+};
+
+// Error bookkeeping (per thread).
+void set_cuda_error(cudaError_t e, const char *what);
+corr_status check_launch(const char *what);
+
+#define CORR_CUDA_TRY(expr)                                  \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) {                             \
+            ::corr::set_cuda_error(_e, #expr);               \
+            return CORR_ECUDA;                               \
+        }                                                    \
+    } while (0)
+
+// Kernel launchers (return CORR_OK or an error status).
+corr_status launch_fengine(const Handle &h, const void *volt, const float *scale, void *out,
+                           cudaStream_t st);
+corr_status launch_fengine_power(const Handle &h, const void *volt, float *power, cudaStream_t st);
+corr_status launch_xengine_cudacore(const Handle &h, const void *chan_in, const float2 *gains,
+                                    bool store, cudaStream_t st);
+corr_status launch_xengine_tc(const Handle &h, const void *chan_in, const float2 *gains, bool store,
+                              cudaStream_t st);
+corr_status launch_dump(const Handle &h, cudaStream_t st);
+size_t backward_workspace_bytes(const Handle &h);
+corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const float2 *chan_in,
+                               const float2 *gains, float2 *grad_chan, float2 *grad_gains, float2 *ws,
+                               cudaStream_t st);
+bool fengine_supported(int n_chan);
+
+// Bounded-wait iteration limit for device-side spins (mbarrier waits).
+constexpr long long kSpinLimit = 1LL << 26;
+
+}  // namespace corr
