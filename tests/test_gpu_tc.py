@@ -1,0 +1,106 @@
+"""Parity of the tcgen05 tensor-core X-engine (through the C ABI) with the FP64
+oracle: INT8 bit-exact, FP16 within its stated tolerance; ragged sizes span
+several tiles, several 512-spectrum INT32 folds and partial pipeline stages."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_1305_5639_gb300 import api
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def norm_err(V, Vref, n_in):
+    i, j = oracle.tri_pairs(n_in)
+    aut = np.abs(Vref[..., oracle.packed_index(np.arange(n_in), np.arange(n_in))])
+    e = np.abs(V - Vref) / np.sqrt(aut[..., i] * aut[..., j])
+    return float(np.max(e)), float(np.sqrt(np.mean(e ** 2)))
+
+
+@pytest.mark.parametrize("n_in,K,n_chan", [
+    (128, 64, 1),      # one diagonal tile, one stage
+    (256, 640, 2),     # 3 tiles, two INT32 folds (512 + 128 spectra)
+    (200, 100, 3),     # ragged inputs, K not a multiple of 8 (scalar loads)
+    (130, 1032, 1),    # 2 x 2 blocks with a 2-input tail, 3 folds, partial last stage
+    (1, 8, 2),         # a single input
+    (384, 136, 1),     # 6 tiles
+])
+def test_tc_int8_bit_exact(cuda_ok, n_in, K, n_chan):
+    X = synth.chan_int8(n_chan, n_in, K, seed=n_in + K)
+    c = api.Correlator(n_in, 1, n_chan, K, precision="int8", xengine="tcgen05")
+    c.xengine(torch.from_numpy(X).to(DEV))
+    V = c.accum().cpu().numpy().astype(np.int64)
+    c.check_status()
+    assert np.array_equal(V, oracle.cmac(X))
+    c.close()
+
+
+def test_tc_int8_extreme_values_exact(cuda_ok):
+    """All samples at +-127 for 4096 spectra: autos reach 2 * 127^2 * 4096, far
+    beyond 2^24, and each 512-spectrum FP32 partial reaches its bound."""
+    n_in, K = 160, 4096
+    X = np.empty((1, n_in, K, 2), np.int8)
+    rng = np.random.default_rng(0)
+    X[...] = np.where(rng.random((1, n_in, K, 2)) < 0.5, 127, -127)
+    X[0, :8] = 127
+    X[0, 8:16] = -127
+    c = api.Correlator(n_in, 1, 1, K, precision="int8", xengine="tcgen05")
+    c.xengine(torch.from_numpy(X).to(DEV))
+    V = c.accum().cpu().numpy().astype(np.int64)
+    assert np.array_equal(V, oracle.cmac(X))
+    c.close()
+
+
+def test_tc_int8_equals_cudacore_and_accumulates(cuda_ok):
+    n_in, K, n_chan = 300, 520, 4
+    X1 = synth.chan_int8(n_chan, n_in, K, seed=1)
+    X2 = synth.chan_int8(n_chan, n_in, K, seed=2)
+    out = []
+    for eng in ("tcgen05", "cudacore"):
+        c = api.Correlator(n_in, 1, n_chan, K, precision="int8", xengine=eng)
+        c.xengine(torch.from_numpy(X1).to(DEV))
+        c.xengine(torch.from_numpy(X2).to(DEV))  # second call adds into the accumulator
+        out.append(c.accum().cpu().numpy())
+        c.close()
+    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0].astype(np.int64), oracle.cmac(X1) + oracle.cmac(X2))
+
+
+def test_tc_int8_deterministic(cuda_ok):
+    n_in, K = 256, 256
+    X = torch.from_numpy(synth.chan_int8(2, n_in, K, seed=5)).to(DEV)
+    c = api.Correlator(n_in, 1, 2, K, precision="int8")
+    c.xengine(X)
+    a = c.accum()
+    c.reset()
+    c.xengine(X)
+    b = c.accum()
+    assert torch.equal(a, b)
+    c.close()
+
+
+@pytest.mark.parametrize("n_in,K,n_chan", [(128, 256, 2), (250, 200, 2), (70, 33, 1)])
+def test_tc_fp16_plain(cuda_ok, n_in, K, n_chan):
+    X = synth.chan_sources(n_chan, n_in, K, n_src=3, seed=3, src_amp=0.1)
+    c = api.Correlator(n_in, 1, n_chan, K, precision="fp16")
+    c.xengine(torch.from_numpy(X).to(DEV))
+    V = c.accum().cpu().numpy().astype(np.complex128)
+    emax, erms = norm_err(V, oracle.cmac(X), n_in)
+    assert emax <= 2e-3, (emax, erms)
+    c.close()
+
+
+def test_tc_fp16_gains(cuda_ok):
+    n_in, K, n_chan = 140, 128, 2
+    X = synth.chan_sources(n_chan, n_in, K, n_src=3, seed=8, src_amp=0.1)
+    g = synth.gains(n_in, seed=8)
+    c = api.Correlator(n_in, 1, n_chan, K, precision="fp16")
+    c.xengine(torch.from_numpy(X).to(DEV), torch.from_numpy(g).to(DEV))
+    V = c.accum().cpu().numpy().astype(np.complex128)
+    ref = oracle.apply_gains(oracle.cmac(X), g, n_in)
+    emax, _ = norm_err(V, ref, n_in)
+    assert emax <= 2e-3
+    c.close()
