@@ -104,18 +104,21 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(n_ant, n_pol, N, K, seed=0, n_chan_sample=2, spectra_sample=None):
+def cpu_oracle_sample(n_ant, n_pol, N, K, seed=0, n_chan_sample=2, spectra_sample=None, volt=None):
     """Time the FP64 oracle on a bounded sample of the workload: the direct DFT of
     `n_chan_sample` channels for every input over `spectra_sample` spectra, their
-    int8 re-packing, and the triple-loop CMAC of those channels. Returns
+    int8 re-packing, and the triple-loop CMAC of those channels. `volt` (the raw
+    int8 voltages, [n_in, K * N, 2]) is generated if not given. Returns
     (cMAC/s, seconds, cores, description)."""
     import oracle
     import synth
 
     Ks = K if spectra_sample is None else spectra_sample
-    v = synth.volt_int8(n_ant, n_pol, N, Ks, seed=seed)
+    if volt is None:
+        volt = synth.volt_int8(n_ant, n_pol, N, Ks, seed=seed)
+    v = volt[:, : Ks * N]
     n_in = n_ant * n_pol
-    bins = np.arange(n_chan_sample) * (N // n_chan_sample) + 3
+    bins = (np.arange(n_chan_sample) * (N // n_chan_sample) + 3 + seed) % N
     scale = np.full(N, 1.0 / np.sqrt(N), np.float32)
     oracle.build()
     t0 = time.perf_counter()
@@ -125,25 +128,26 @@ def cpu_oracle_sample(n_ant, n_pol, N, K, seed=0, n_chan_sample=2, spectra_sampl
     dt = time.perf_counter() - t0
     cmacs = n_chan_sample * (n_in * (n_in + 1) // 2) * Ks
     cores = len(os.sched_getaffinity(0))
-    desc = (f"oracle DFT+requant+CMAC of {n_chan_sample} of {N} channels, all {n_in} inputs, "
-            f"{Ks} of {K} spectra")
+    desc = (f"oracle direct DFT + requant + triple-loop CMAC of {n_chan_sample} of {N} channels, all {n_in} "
+            f"inputs, {Ks} of {K} spectra (OpenMP over frames / channels)")
     return cmacs / dt, dt, cores, desc
 
 
 def run_reference(args):
+    """The oracle as it stands, on the host cores, one bounded sample per step."""
+    import synth
+
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     n_ant, n_pol, N, K = WORKLOADS[args.workload]
-    n_in = n_ant * n_pol
-    Ks = max(64, K // 16)
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm state; warm-up steps are not repeated
+    volt = synth.volt_int8(n_ant, n_pol, N, K, seed=0)
     rates, secs = [], []
-    for s in range(args.steps):
-        r, dt, cores, desc = cpu_oracle_sample(n_ant, n_pol, N, K, seed=s, n_chan_sample=1, spectra_sample=Ks)
-        rates.append(r)
-        secs.append(dt)
+    for s in range(args.warmup + args.steps):
+        r, dt, cores, desc = cpu_oracle_sample(n_ant, n_pol, N, K, seed=s, n_chan_sample=1, volt=volt)
+        if s >= args.warmup:
+            rates.append(r)
+            secs.append(dt)
     v = float(np.mean(rates))
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "cMAC/s", "n_gpus": ws, "steps": args.steps,
@@ -189,7 +193,6 @@ def run_ours(args):
 
     volt_h = synth.volt_int8(n_ant, n_pol, N, K, seed=rank)
     volt_pin = torch.from_numpy(volt_h).pin_memory()
-    del volt_h
     volt = volt_pin.to(dev, non_blocking=False)
     corr = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine=args.xengine)
     chan = corr.chan_buffer()
@@ -304,7 +307,7 @@ def run_ours(args):
                 "traffic": None, "kernel": "X-engine INT8 CUDA-core dp4a"}
     cpu = None
     if ws == 1 and not args.no_cpu:
-        r, dt, cores, desc = cpu_oracle_sample(n_ant, n_pol, N, K, n_chan_sample=1, spectra_sample=max(64, K // 16))
+        r, dt, cores, desc = cpu_oracle_sample(n_ant, n_pol, N, K, n_chan_sample=2, volt=volt_h)
         cpu = {"value": r, "unit": "cMAC/s", "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
     launches = 3  # F-engine, X-engine, dump per step (the calibration power pass is outside the timed region)
     line = {

@@ -157,11 +157,17 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
     ok = cudaMemset(h.acc, 0, acc_bytes) == cudaSuccess && cudaMemset(h.vis64, 0, nvis * sizeof(double2)) == cudaSuccess &&
          cudaMemset(h.status, 0, sizeof(int32_t)) == cudaSuccess;
     if (ok && h.twiddle) {
-        // W_N^m = exp(-j 2 pi m / N) in double, rounded once to float
+        // F-engine twiddles W_N^(t k1) = exp(-j 2 pi t k1 / N) for the N = T x T split,
+        // laid out [k1][t]; computed in double, rounded once to float
+        int T = 1;
+        while (T * T < n_chan) T *= 2;
         std::vector<float2> tw((size_t)n_chan);
-        for (int m = 0; m < n_chan; ++m) {
-            double ang = 2.0 * M_PI * (double)m / (double)n_chan;
-            tw[(size_t)m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+        for (int k1 = 0; k1 < T; ++k1) {
+            for (int t = 0; t < T; ++t) {
+                const int m = (t * k1) % n_chan;
+                const double ang = 2.0 * M_PI * (double)m / (double)n_chan;
+                tw[(size_t)k1 * T + t] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+            }
         }
         ok = cudaMemcpy(h.twiddle, tw.data(), sizeof(float2) * (size_t)n_chan, cudaMemcpyHostToDevice) == cudaSuccess;
     }

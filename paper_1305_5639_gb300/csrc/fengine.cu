@@ -5,7 +5,7 @@
 // Each N = T x T point FFT is computed by T threads in two register passes
 // (four-step / Cooley-Tukey split n = t + T m, k = k1 + T k2):
 //   pass 1: thread t holds x[t + T m], m < T, and computes the T-point DFT over m;
-//           the result is multiplied by W_N^(t k1) (twiddle table in shared memory)
+//           the result is multiplied by W_N^(t k1) (twiddle table, L1-resident)
 //   exchange through shared memory (padded rows, conflict-free)
 //   pass 2: thread k1 holds Y[t][k1], t < T, and computes the T-point DFT over t,
 //           giving X[k1 + T k2].
@@ -29,30 +29,40 @@ struct FCfg {
     static constexpr int T = isqrt_pow4(N);
     static_assert(T * T == N, "N must be a power of 4");
     static constexpr int G = kThreads / T;  // FFTs in flight per CTA
-    static constexpr int EXS = T + 1;       // exchange row stride (float2)
+    static constexpr int EXS = T + 1;       // exchange row stride (floats; Re and Im exchanged in turn)
     // spectra per CTA
     static constexpr int SB = MODE == kRequant ? 16 : (MODE == kFloatOut ? 8 : 16);
     static_assert(SB % (G < SB ? G : SB) == 0 || G >= SB, "");
     // staging row stride in 32-bit words
     static constexpr int ROWW = MODE == kRequant ? SB / 2 + 1 : (MODE == kFloatOut ? 2 * SB + 2 : 0);
-    static constexpr size_t tw_bytes = sizeof(float2) * N;
-    static constexpr size_t ex_bytes = sizeof(float2) * (size_t)G * T * EXS;
-    static constexpr size_t sc_bytes = sizeof(float) * N;
+    static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * T * EXS;
+    static constexpr size_t pw_bytes = MODE == kPower ? sizeof(float) * N : 0;
     static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW;
-    static constexpr size_t smem = tw_bytes + ex_bytes + sc_bytes + st_bytes;
+    static constexpr size_t smem = ex_bytes + pw_bytes + st_bytes;
 };
+
+// 1.5 * 2^23: adding it to |v| <= 2^22 rounds v to the nearest integer (ties to
+// even, the FP32 adder's rounding) and leaves that integer in the low mantissa bits.
+constexpr float kMagic = 12582912.0f;
 
 __device__ __forceinline__ uint32_t pack_q(float2 v, float sc) {
     // Re-pack to int8: clamp(S * scale) to [-127, 127], round half to even.
-    float re = fminf(fmaxf(v.x * sc, -127.0f), 127.0f);
-    float im = fminf(fmaxf(v.y * sc, -127.0f), 127.0f);
-    int qr = __float2int_rn(re);
-    int qi = __float2int_rn(im);
-    return (uint32_t)(qr & 0xff) | ((uint32_t)(qi & 0xff) << 8);
+    const float re = fminf(fmaxf(v.x * sc, -127.0f), 127.0f) + kMagic;
+    const float im = fminf(fmaxf(v.y * sc, -127.0f), 127.0f) + kMagic;
+    // low byte of each result is the two's-complement int8 code
+    return __byte_perm(__float_as_uint(re), __float_as_uint(im), 0x0040);
+}
+
+// complex int8 sample (16 bits: re in the low byte) -> float2, exactly:
+// (0x4B400000 | (x + 128)) is the float 12582912 + x + 128.
+__device__ __forceinline__ float2 i8_to_f2(uint32_t w) {
+    const uint32_t u = w ^ 0x8080u;
+    return make_float2(__uint_as_float(__byte_perm(u, 0x4B400000u, 0x7650)) - (kMagic + 128.0f),
+                       __uint_as_float(__byte_perm(u, 0x4B400000u, 0x7651)) - (kMagic + 128.0f));
 }
 
 template <int N, bool I8, int MODE>
-__global__ void __launch_bounds__(kThreads) k_fengine(const void *__restrict__ volt,
+__global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 : 3) k_fengine(const void *__restrict__ volt,
                                                       const float *__restrict__ scale,
                                                       void *__restrict__ out,
                                                       double *__restrict__ power, int n_in, int K,
@@ -60,24 +70,20 @@ __global__ void __launch_bounds__(kThreads) k_fengine(const void *__restrict__ v
     using C = FCfg<N, I8, MODE>;
     constexpr int T = C::T, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *twid = reinterpret_cast<float2 *>(smem_raw);                        // [T k1][T t]
-    float2 *ex = reinterpret_cast<float2 *>(smem_raw + C::tw_bytes);            // [G][T][EXS]
-    float *scs = reinterpret_cast<float *>(smem_raw + C::tw_bytes + C::ex_bytes);  // [N]
-    uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::tw_bytes + C::ex_bytes + C::sc_bytes);
+    float *ex = reinterpret_cast<float *>(smem_raw);                                 // [G][T][EXS]
+    float *scs = reinterpret_cast<float *>(smem_raw + C::ex_bytes);                  // [N] (power)
+    uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::ex_bytes + C::pw_bytes);  // staging
 
     const int i = blockIdx.y;
     const int a0 = blockIdx.x * SB;
-    for (int m = threadIdx.x; m < N; m += kThreads) {
-        int k1 = m / T, t = m % T;
-        twid[m] = tw_glob[(t * k1) % N];
-        if constexpr (MODE == kRequant) scs[m] = scale[m];
-        if constexpr (MODE == kPower) scs[m] = 0.0f;
+    if constexpr (MODE == kPower) {
+        for (int m = threadIdx.x; m < N; m += kThreads) scs[m] = 0.0f;
+        __syncthreads();
     }
-    __syncthreads();
 
     const int g = threadIdx.x / T;
     const int t = threadIdx.x % T;
-    float2 *exg = ex + (size_t)g * T * EXS;
+    float *exg = ex + (size_t)g * T * EXS;
     float pw[T];
     if constexpr (MODE == kPower) {
 #pragma unroll
@@ -92,11 +98,11 @@ __global__ void __launch_bounds__(kThreads) k_fengine(const void *__restrict__ v
         // ---- pass 1: thread t takes x[t + T m]
         const size_t base = ((size_t)i * K + (size_t)(valid ? a : 0)) * N + t;
         if constexpr (I8) {
-            const char2 *src = reinterpret_cast<const char2 *>(volt) + base;
+            const unsigned short *src = reinterpret_cast<const unsigned short *>(volt) + base;
 #pragma unroll
             for (int m = 0; m < T; ++m) {
-                char2 c = valid ? __ldg(src + (size_t)T * m) : make_char2(0, 0);
-                v[m] = make_float2((float)c.x, (float)c.y);
+                const uint32_t w = valid ? (uint32_t)__ldg(src + (size_t)T * m) : 0u;
+                v[m] = i8_to_f2(w);
             }
         } else {
             const float2 *src = reinterpret_cast<const float2 *>(volt) + base;
@@ -106,14 +112,26 @@ __global__ void __launch_bounds__(kThreads) k_fengine(const void *__restrict__ v
         fft_dif<T>(v);  // v[bitrev(k1)] = Y[t][k1]
         sfor<0, T>([&](auto K1) {
             constexpr int k1 = decltype(K1)::value;
-            float2 y = v[bitrev(k1, ilog2(T))];
-            if constexpr (k1 != 0) y = cmul(y, twid[k1 * T + t]);
-            exg[k1 * EXS + t] = y;
+            // twiddle W_N^(t k1), table laid out [k1][t]
+            if constexpr (k1 != 0) v[bitrev(k1, ilog2(T))] = cmul(v[bitrev(k1, ilog2(T))], __ldg(tw_glob + k1 * T + t));
+        });
+        // ---- exchange (Re, then Im; the other half stays in place) and pass 2:
+        // thread t now plays k1 = t and takes Y[tt][k1]
+        sfor<0, T>([&](auto K1) {
+            constexpr int k1 = decltype(K1)::value;
+            exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T))].x;
         });
         if constexpr (T <= 32) __syncwarp(); else __syncthreads();
-        // ---- pass 2: thread t now plays k1 = t and takes Y[tt][k1]
 #pragma unroll
-        for (int tt = 0; tt < T; ++tt) v[tt] = exg[t * EXS + tt];
+        for (int tt = 0; tt < T; ++tt) v[tt].x = exg[t * EXS + tt];
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+        sfor<0, T>([&](auto K1) {
+            constexpr int k1 = decltype(K1)::value;
+            exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T))].y;
+        });
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+#pragma unroll
+        for (int tt = 0; tt < T; ++tt) v[tt].y = exg[t * EXS + tt];
         if constexpr (T <= 32) __syncwarp(); else __syncthreads();
         fft_dif<T>(v);  // v[bitrev(k2)] = X[t + T k2]
         if (valid) {
@@ -122,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) k_fengine(const void *__restrict__ v
                 const int k = t + T * k2;
                 float2 x = v[bitrev(k2, ilog2(T))];
                 if constexpr (MODE == kRequant) {
-                    uint32_t q = pack_q(x, scs[k]);
+                    uint32_t q = pack_q(x, __ldg(scale + k));
                     reinterpret_cast<uint16_t *>(stg)[(size_t)k * (2 * ROWW) + s] = (uint16_t)q;
                 } else if constexpr (MODE == kFloatOut) {
                     reinterpret_cast<float2 *>(stg)[(size_t)k * (ROWW / 2) + s] = x;

@@ -20,7 +20,7 @@ struct Handle {
     bool acc_zero = true;        // accumulator known to be all-zero (X-engine may store instead of add)
     int64_t acc_spectra = 0;     // spectra accumulated since the last dump (INT8 overflow guard)
     double2 *vis64 = nullptr;    // FP64 long-integration buffer [n_chan][B]
-    float2 *twiddle = nullptr;   // W_N^m = exp(-j 2 pi m / N), m in [0, N)
+    float2 *twiddle = nullptr;   // F-engine twiddles W_N^(t k1), [k1][t], N = T x T
     int32_t *status = nullptr;   // device status word (0 ok, else CORR_* code set by a kernel)
     double *power64 = nullptr;   // [n_chan] scratch for corr_fengine_power
     float2 *bwd_ws = nullptr;    // dg partials for corr_backward (allocated on first use)

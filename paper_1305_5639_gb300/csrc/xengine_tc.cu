@@ -18,10 +18,12 @@
 // FP16: inputs rounded to FP16, FP32 accumulation over the whole integration, with
 // the accumulator double-buffered in TMEM so the epilogue overlaps the next tile.
 //
-// Warp roles (288 threads, one persistent CTA per SM):
-//   warps 0-3  producers: global loads -> FP16 planes in 128B-swizzled K-major smem
-//   warp  4    TMEM allocator + single-thread MMA issuer
-//   warps 5-8  epilogue: tcgen05.ld -> (INT32 fold | gains) -> packed global store
+// Warp roles (544 threads, one persistent CTA per SM):
+//   warps 0-7   producers: global loads (one stage ahead, in registers) -> FP16
+//               planes in 128B-swizzled K-major shared memory
+//   warp  8     TMEM allocator + single-thread MMA issuer
+//   warps 9-16  epilogue, two warps per TMEM lane quarter (each half the columns):
+//               tcgen05.ld -> (INT32 fold | gains) -> packed global store
 // Every mbarrier wait is bounded; on time-out the CTA records CORR_ETIMEOUT and
 // all roles leave their loops.
 #include <cuda_fp16.h>
@@ -39,7 +41,10 @@ constexpr int NBLK = 5;                    // A_re, A_im, B_im, B_re, B_nim
 constexpr int STAGE_BYTES = NBLK * BLK;    // 80 KB
 constexpr int NSTAGE = 2;
 constexpr int CHUNK_KB = 8;                // INT8 flush every 8 stages = 512 spectra
-constexpr int NPROD = 128, NEPI = 128;
+constexpr int NPW = 8;                     // producer warps
+constexpr int MMA_WARP = NPW;              // TMEM allocator + MMA issuer
+constexpr int NEW = 8;                     // epilogue warps (two per TMEM lane quarter)
+constexpr int NPROD = 32 * NPW, NEPI = 32 * NEW;
 constexpr int NTHREADS = NPROD + 32 + NEPI;
 constexpr int OFF_ARE = 0, OFF_AIM = BLK, OFF_BIM = 2 * BLK, OFF_BRE = 3 * BLK, OFF_BNIM = 4 * BLK;
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
@@ -135,8 +140,14 @@ __device__ __forceinline__ uint4 load_f2_pair(const float2 *row, int s, int K) {
     return make_uint4(__float_as_uint(a.x), __float_as_uint(a.y), __float_as_uint(b.x), __float_as_uint(b.y));
 }
 
+// One pipeline stage of input data held in registers by a producer thread:
+// 4 chunks (16 B = 8 spectra of complex int8) of the J block and 4 of the I block.
+struct StageRegs {
+    uint4 j[4], i[4];
+};
+
 template <int MODE, bool VEC>
-__global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
+__global__ void __maxnreg__(120) k_xeng_tc(const XParams p) {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -165,7 +176,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == MMA_WARP) {
         tc::tmem_alloc(tc::smem_u32(tmem_slot), 512);
         tc::tmem_relinquish();
     }
@@ -174,114 +185,138 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int nkb = (p.K + KB - 1) / KB;
+    // this CTA's items are blockIdx.x + it * gridDim.x; its stages are (it, kb) in order
+    const long long my_items = (p.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const long long n_stages = my_items * nkb;
 
-    if (warp < 4) {
+    if (warp < NPW) {
         // ------------------------------------------------------------ producers
         const int t = threadIdx.x;
-        const int c = t & 7;  // 16-byte chunk within a 128-byte fp16 row
-        int stage = 0;
-        uint32_t phase = 0;
-        bool alive = true;
-        for (long long item = blockIdx.x; item < p.n_items && alive; item += gridDim.x) {
-            int chan, bi, bj;
-            decode_item(item, p.n_tiles, chan, bi, bj);
-            const bool diag = bi == bj;
-            const int I0 = bi * TILE, J0 = bj * TILE;
-            for (int kb = 0; kb < nkb && alive; ++kb) {
-                const int s0 = kb * KB;
-                if constexpr (MODE == kInt8) {
-                    const char2 *X = static_cast<const char2 *>(p.X) + (size_t)chan * p.n_in * p.K;
-                    uint4 vj[8], vi[8];
+        const int c = t & 7;   // 16-byte chunk of a 128-byte fp16 row (8 spectra)
+        const int r0 = t >> 3; // first row; rows r0 + 32 q, q < 4
+        auto coords = [&](long long n, int &chan, int &I0, int &J0, bool &diag, int &s0) {
+            const long long it = n / nkb;
+            const int kb = (int)(n - it * nkb);
+            int bi, bj;
+            decode_item(blockIdx.x + it * gridDim.x, p.n_tiles, chan, bi, bj);
+            I0 = bi * TILE;
+            J0 = bj * TILE;
+            diag = bi == bj;
+            s0 = kb * KB;
+        };
+        if constexpr (MODE == kInt8) {
+            auto load = [&](long long n, StageRegs &R) {
+                int chan, I0, J0, s0;
+                bool diag;
+                coords(n, chan, I0, J0, diag, s0);
+                const char2 *X = static_cast<const char2 *>(p.X) + (size_t)chan * p.n_in * p.K;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int r = (t >> 3) + 16 * q;
-                        const int gj = J0 + r, gi = I0 + r;
-                        vj[q] = gj < p.n_in ? load_i8_chunk<VEC>(X + (size_t)gj * p.K, s0 + 8 * c, p.K)
-                                            : make_uint4(0, 0, 0, 0);
-                        vi[q] = (!diag && gi < p.n_in) ? load_i8_chunk<VEC>(X + (size_t)gi * p.K, s0 + 8 * c, p.K)
-                                                       : make_uint4(0, 0, 0, 0);
-                    }
-                    if (!tc::mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.status)) {
-                        alive = false;
-                        break;
-                    }
-                    const uint32_t st = sbase + stage * STAGE_BYTES;
+                for (int q = 0; q < 4; ++q) {
+                    const int r = r0 + 32 * q;
+                    const int gj = J0 + r, gi = I0 + r;
+                    R.j[q] = gj < p.n_in ? load_i8_chunk<VEC>(X + (size_t)gj * p.K, s0 + 8 * c, p.K)
+                                         : make_uint4(0, 0, 0, 0);
+                    R.i[q] = (!diag && gi < p.n_in) ? load_i8_chunk<VEC>(X + (size_t)gi * p.K, s0 + 8 * c, p.K)
+                                                    : make_uint4(0, 0, 0, 0);
+                }
+            };
+            auto consume = [&](long long n, const StageRegs &R) -> bool {
+                const int slot = (int)(n % NSTAGE);
+                const uint32_t ph = (uint32_t)((n / NSTAGE) & 1);
+                if (!tc::mbar_wait(empty_bar(slot), ph ^ 1u, abort_flag, p.status)) return false;
+                int chan, I0, J0, s0;
+                bool diag;
+                coords(n, chan, I0, J0, diag, s0);
+                const uint32_t st = sbase + slot * STAGE_BYTES;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int r = (t >> 3) + 16 * q;
-                        const uint32_t o = swz(r, c);
-                        uint4 re, im, nim;
-                        cvt_i8(vj[q], re, im, nim);
-                        st_shared_v4(st + OFF_BIM + o, im);
-                        st_shared_v4(st + OFF_BRE + o, re);
-                        st_shared_v4(st + OFF_BNIM + o, nim);
-                        if (!diag) {
-                            cvt_i8(vi[q], re, im, nim);
-                            st_shared_v4(st + OFF_ARE + o, re);
-                            st_shared_v4(st + OFF_AIM + o, im);
-                        }
-                    }
-                } else {
-                    const float2 *X = static_cast<const float2 *>(p.X) + (size_t)chan * p.n_in * p.K;
-                    if (!tc::mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.status)) {
-                        alive = false;
-                        break;
-                    }
-                    const uint32_t st = sbase + stage * STAGE_BYTES;
-#pragma unroll 2
-                    for (int q = 0; q < 8; ++q) {
-                        const int r = (t >> 3) + 16 * q;
-                        const uint32_t o = swz(r, c);
-                        const int s = s0 + 8 * c;
-#pragma unroll
-                        for (int side = 0; side < 2; ++side) {
-                            if (side == 1 && diag) break;
-                            const int g = (side == 0 ? J0 : I0) + r;
-                            uint32_t re[4], im[4], nim[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                uint4 v = g < p.n_in ? load_f2_pair<VEC>(X + (size_t)g * p.K, s + 2 * e, p.K)
-                                                     : make_uint4(0, 0, 0, 0);
-                                cvt_f2(v, re[e], im[e], nim[e]);
-                            }
-                            const uint4 R = make_uint4(re[0], re[1], re[2], re[3]);
-                            const uint4 M = make_uint4(im[0], im[1], im[2], im[3]);
-                            if (side == 0) {
-                                st_shared_v4(st + OFF_BIM + o, M);
-                                st_shared_v4(st + OFF_BRE + o, R);
-                                st_shared_v4(st + OFF_BNIM + o, make_uint4(nim[0], nim[1], nim[2], nim[3]));
-                            } else {
-                                st_shared_v4(st + OFF_ARE + o, R);
-                                st_shared_v4(st + OFF_AIM + o, M);
-                            }
-                        }
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t o = swz(r0 + 32 * q, c);
+                    uint4 re, im, nim;
+                    cvt_i8(R.j[q], re, im, nim);
+                    st_shared_v4(st + OFF_BIM + o, im);
+                    st_shared_v4(st + OFF_BRE + o, re);
+                    st_shared_v4(st + OFF_BNIM + o, nim);
+                    if (!diag) {
+                        cvt_i8(R.i[q], re, im, nim);
+                        st_shared_v4(st + OFF_ARE + o, re);
+                        st_shared_v4(st + OFF_AIM + o, im);
                     }
                 }
                 tc::fence_proxy_async_smem();
-                tc::mbar_arrive(full_bar(stage));
-                if (++stage == NSTAGE) {
-                    stage = 0;
-                    phase ^= 1u;
+                tc::mbar_arrive(full_bar(slot));
+                return true;
+            };
+            // software pipeline: the loads of stage n + 1 are in flight while stage n is converted
+            StageRegs A, Bq;
+            if (n_stages > 0) load(0, A);
+            for (long long n = 0; n < n_stages; n += 2) {
+                if (n + 1 < n_stages) load(n + 1, Bq);
+                if (!consume(n, A)) break;
+                if (n + 1 >= n_stages) break;
+                if (n + 2 < n_stages) load(n + 2, A);
+                if (!consume(n + 1, Bq)) break;
+            }
+        } else {
+            for (long long n = 0; n < n_stages; ++n) {
+                int chan, I0, J0, s0;
+                bool diag;
+                coords(n, chan, I0, J0, diag, s0);
+                const float2 *X = static_cast<const float2 *>(p.X) + (size_t)chan * p.n_in * p.K;
+                // convert to fp16 in registers first (loads in flight before the slot is free)
+                uint4 hre[2][4], him[2][4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                    for (int side = 0; side < 2; ++side) {
+                        const int g = (side == 0 ? J0 : I0) + r0 + 32 * q;
+                        const bool ok = g < p.n_in && (side == 0 || !diag);
+                        uint32_t re[4], im[4], nim[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            uint4 v = ok ? load_f2_pair<VEC>(X + (size_t)g * p.K, s0 + 8 * c + 2 * e, p.K)
+                                         : make_uint4(0, 0, 0, 0);
+                            cvt_f2(v, re[e], im[e], nim[e]);
+                        }
+                        hre[side][q] = make_uint4(re[0], re[1], re[2], re[3]);
+                        him[side][q] = make_uint4(im[0], im[1], im[2], im[3]);
+                    }
                 }
+                const int slot = (int)(n % NSTAGE);
+                const uint32_t ph = (uint32_t)((n / NSTAGE) & 1);
+                if (!tc::mbar_wait(empty_bar(slot), ph ^ 1u, abort_flag, p.status)) break;
+                const uint32_t st = sbase + slot * STAGE_BYTES;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t o = swz(r0 + 32 * q, c);
+                    const uint4 M = him[0][q];
+                    st_shared_v4(st + OFF_BIM + o, M);
+                    st_shared_v4(st + OFF_BRE + o, hre[0][q]);
+                    st_shared_v4(st + OFF_BNIM + o,
+                                 make_uint4(M.x ^ 0x80008000u, M.y ^ 0x80008000u, M.z ^ 0x80008000u, M.w ^ 0x80008000u));
+                    if (!diag) {
+                        st_shared_v4(st + OFF_ARE + o, hre[1][q]);
+                        st_shared_v4(st + OFF_AIM + o, him[1][q]);
+                    }
+                }
+                tc::fence_proxy_async_smem();
+                tc::mbar_arrive(full_bar(slot));
             }
         }
-    } else if (warp == 4) {
+    } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t IDESC = tc::idesc_f16(128, 256);
-            int stage = 0;
-            uint32_t phase = 0;
             uint32_t ae_phase[2] = {0, 0};
-            int nbuf_item = 0;
+            long long n = 0;  // stage counter, same sequence as the producers
             bool alive = true;
-            for (long long item = blockIdx.x; item < p.n_items && alive; item += gridDim.x) {
+            for (long long it = 0; it < my_items && alive; ++it) {
                 int chan, bi, bj;
-                decode_item(item, p.n_tiles, chan, bi, bj);
+                decode_item(blockIdx.x + it * gridDim.x, p.n_tiles, chan, bi, bj);
                 const bool diag = bi == bj;
-                const int buf = MODE == kInt8 ? 0 : (nbuf_item & 1);
+                const int buf = MODE == kInt8 ? 0 : (int)(it & 1);
                 const uint32_t d_tmem = tmem + (uint32_t)(buf * 256);
                 const int chunk = MODE == kInt8 ? CHUNK_KB : nkb;
-                for (int kb = 0; kb < nkb && alive; ++kb) {
+                for (int kb = 0; kb < nkb; ++kb, ++n) {
                     const int kin = kb % chunk;
                     if (kin == 0) {
                         // the epilogue has released this accumulator
@@ -292,12 +327,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
                         ae_phase[buf] ^= 1u;
                         tc::tc_fence_after();
                     }
-                    if (!tc::mbar_wait(full_bar(stage), phase, abort_flag, p.status)) {
+                    const int slot = (int)(n % NSTAGE);
+                    if (!tc::mbar_wait(full_bar(slot), (uint32_t)((n / NSTAGE) & 1), abort_flag, p.status)) {
                         alive = false;
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t st = sbase + stage * STAGE_BYTES;
+                    const uint32_t st = sbase + slot * STAGE_BYTES;
                     const uint32_t a_re = st + (diag ? OFF_BRE : OFF_ARE);
                     const uint32_t a_im = st + (diag ? OFF_BIM : OFF_AIM);
 #pragma unroll
@@ -307,14 +343,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
                                     (kin > 0 || k > 0) ? 1u : 0u);
                         tc::mma_f16(d_tmem, tc::desc_sw128(a_im + koff), tc::desc_sw128(st + OFF_BIM + koff), IDESC, 1u);
                     }
-                    tc::mma_commit(empty_bar(stage));
-                    if (++stage == NSTAGE) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
+                    tc::mma_commit(empty_bar(slot));
                     if (kin == chunk - 1 || kb == nkb - 1) tc::mma_commit(accf_bar(buf));
                 }
-                ++nbuf_item;
             }
             // drain: every MMA issued must have completed before TMEM is released
             tc::mma_commit(drain_bar);
@@ -323,18 +354,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        const int wq = warp & 3;              // TMEM lane quarter of this warp
-        const int m = wq * 32 + lane;         // tile row
+        const int ew = warp - (MMA_WARP + 1);  // 0..7
+        const int wq = warp & 3;               // TMEM lane quarter this warp may access
+        const int h = ew >> 2;                 // column half: j in [64 h, 64 h + 64)
+        const int m = wq * 32 + lane;          // tile row = TMEM lane
         const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
         uint32_t af_phase[2] = {0, 0};
-        int nbuf_item = 0;
         bool alive = true;
-        for (long long item = blockIdx.x; item < p.n_items && alive; item += gridDim.x) {
+        for (long long it = 0; it < my_items && alive; ++it) {
             int chan, bi, bj;
-            decode_item(item, p.n_tiles, chan, bi, bj);
+            decode_item(blockIdx.x + it * gridDim.x, p.n_tiles, chan, bi, bj);
             const int I0 = bi * TILE, J0 = bj * TILE;
             const int i = I0 + m;
-            const int buf = MODE == kInt8 ? 0 : (nbuf_item & 1);
+            const int buf = MODE == kInt8 ? 0 : (int)(it & 1);
             const uint32_t d_tmem = tmem + lane_off + (uint32_t)(buf * 256);
             if constexpr (MODE == kInt8) {
                 const uint32_t r_tmem = tmem + lane_off + 256u;
@@ -348,35 +380,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
                     tc::tc_fence_after();
 #pragma unroll 1
                     for (int cb = 0; cb < 8; ++cb) {
-                        uint32_t d[32], r[32];
-                        tc::tmem_ld32(d_tmem + 32u * cb, d);
-                        if (ch > 0) tc::tmem_ld32(r_tmem + 32u * cb, r);
+                        // columns: Re 64h + 16 cb (cb < 4), Im 128 + 64h + 16 (cb - 4)
+                        const uint32_t col = (uint32_t)((cb < 4 ? 0 : 128) + 64 * h + 16 * (cb & 3));
+                        uint32_t d[16], r[16];
+                        tc::tmem_ld16(d_tmem + col, d);
+                        if (ch > 0) tc::tmem_ld16(r_tmem + col, r);
                         tc::tmem_wait_ld();
 #pragma unroll
-                        for (int x = 0; x < 32; ++x) {
+                        for (int x = 0; x < 16; ++x) {
                             int v = __float2int_rn(__uint_as_float(d[x]));
                             r[x] = (uint32_t)((ch > 0 ? (int)r[x] : 0) + v);
                         }
-                        tc::tmem_st32(r_tmem + 32u * cb, r);
+                        tc::tmem_st16(r_tmem + col, r);
                     }
                     tc::tmem_wait_st();
                     tc::tc_fence_before();
                     tc::mbar_arrive(acce_bar(0));
                 }
                 if (!alive) break;
-                // write the tile's INT32 sums: Re in columns 0..127, Im in 128..255 of R
+                // write this tile's INT32 sums (R: Re in columns 0..127, Im in 128..255)
                 int2 *acc = static_cast<int2 *>(p.acc) + (size_t)chan * p.B;
 #pragma unroll 1
                 for (int cb = 0; cb < 4; ++cb) {
-                    uint32_t re[32], im[32];
-                    tc::tmem_ld32(r_tmem + 32u * cb, re);
-                    tc::tmem_ld32(r_tmem + 128u + 32u * cb, im);
+                    uint32_t re[16], im[16];
+                    const uint32_t col = (uint32_t)(64 * h + 16 * cb);
+                    tc::tmem_ld16(r_tmem + col, re);
+                    tc::tmem_ld16(r_tmem + 128u + col, im);
                     tc::tmem_wait_ld();
                     if (i < p.n_in) {
                         int2 *row = acc + (size_t)i * (i + 1) / 2;
 #pragma unroll
-                        for (int x = 0; x < 32; ++x) {
-                            const int j = J0 + cb * 32 + x;
+                        for (int x = 0; x < 16; ++x) {
+                            const int j = J0 + (int)col + x;
                             if (j <= i) {
                                 int2 v = make_int2((int)re[x], (int)im[x]);
                                 if (!p.store) {
@@ -401,15 +436,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
                 if (p.gains && i < p.n_in) gi = __ldg(p.gains + i);
 #pragma unroll 1
                 for (int cb = 0; cb < 4; ++cb) {
-                    uint32_t re[32], im[32];
-                    tc::tmem_ld32(d_tmem + 32u * cb, re);
-                    tc::tmem_ld32(d_tmem + 128u + 32u * cb, im);
+                    uint32_t re[16], im[16];
+                    const uint32_t col = (uint32_t)(64 * h + 16 * cb);
+                    tc::tmem_ld16(d_tmem + col, re);
+                    tc::tmem_ld16(d_tmem + 128u + col, im);
                     tc::tmem_wait_ld();
                     if (i < p.n_in) {
                         float2 *row = acc + (size_t)i * (i + 1) / 2;
 #pragma unroll
-                        for (int x = 0; x < 32; ++x) {
-                            const int j = J0 + cb * 32 + x;
+                        for (int x = 0; x < 16; ++x) {
+                            const int j = J0 + (int)col + x;
                             if (j <= i) {
                                 float2 v = make_float2(__uint_as_float(re[x]), __uint_as_float(im[x]));
                                 if (p.gains) {
@@ -430,14 +466,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
                 tc::tc_fence_before();
                 tc::mbar_arrive(acce_bar(buf));
             }
-            ++nbuf_item;
         }
     }
 
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    if (warp == 4) tc::tmem_dealloc(tmem, 512);
+    if (warp == MMA_WARP) tc::tmem_dealloc(tmem, 512);
 }
 
 template <int MODE, bool VEC>
