@@ -18,7 +18,8 @@
 // FP16: inputs rounded to FP16, FP32 accumulation over the whole integration, with
 // the accumulator double-buffered in TMEM so the epilogue overlaps the next tile.
 //
-// Warp roles (544 threads, one persistent CTA per SM):
+// Warp roles (544 threads, one persistent CTA per SM; 17 warps put 5 warps on one
+// SM sub-partition, whose 16K-register file caps the kernel at 96 registers):
 //   warps 0-7   producers: global loads (one stage ahead, in registers) -> FP16
 //               planes in 128B-swizzled K-major shared memory
 //   warp  8     TMEM allocator + single-thread MMA issuer
@@ -147,7 +148,7 @@ struct StageRegs {
 };
 
 template <int MODE, bool VEC>
-__global__ void __maxnreg__(120) k_xeng_tc(const XParams p) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tc(const XParams p) {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
