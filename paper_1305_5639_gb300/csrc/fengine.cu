@@ -191,26 +191,32 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
     }
 }
 
+// Shape and twiddle table of one F-engine launch.
+struct FShape {
+    int n_in, n_chan, n_spectra;
+    bool i8;
+    const float2 *tw;  // [k1][t] table for n_chan = T x T
+};
+
 template <int N, bool I8, int MODE>
-corr_status launch_one(const Handle &h, const void *volt, const float *scale, void *out, double *power,
+corr_status launch_one(const FShape &f, const void *volt, const float *scale, void *out, double *power,
                        cudaStream_t st) {
     using C = FCfg<N, I8, MODE>;
     auto kern = k_fengine<N, I8, MODE>;
     CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-    dim3 grid((h.n_spectra + C::SB - 1) / C::SB, h.n_in);
-    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, h.n_in, h.n_spectra, h.twiddle);
+    dim3 grid((f.n_spectra + C::SB - 1) / C::SB, f.n_in);
+    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw);
     return check_launch("k_fengine");
 }
 
 template <int MODE>
-corr_status dispatch(const Handle &h, const void *volt, const float *scale, void *out, double *power,
+corr_status dispatch(const FShape &f, const void *volt, const float *scale, void *out, double *power,
                      cudaStream_t st) {
-    const bool i8 = h.precision == CORR_PREC_INT8;
 #define CORR_F_CASE(NN)                                                                  \
     case NN:                                                                             \
-        return i8 ? launch_one<NN, true, MODE>(h, volt, scale, out, power, st)           \
-                  : launch_one<NN, false, MODE>(h, volt, scale, out, power, st);
-    switch (h.n_chan) {
+        return f.i8 ? launch_one<NN, true, MODE>(f, volt, scale, out, power, st)         \
+                    : launch_one<NN, false, MODE>(f, volt, scale, out, power, st);
+    switch (f.n_chan) {
         CORR_F_CASE(16)
         CORR_F_CASE(64)
         CORR_F_CASE(256)
@@ -220,30 +226,37 @@ corr_status dispatch(const Handle &h, const void *volt, const float *scale, void
 #undef CORR_F_CASE
 }
 
+FShape shape_of(const Handle &h) {
+    return FShape{h.n_in, h.n_chan, h.n_spectra, h.precision == CORR_PREC_INT8, h.twiddle};
+}
+
+__global__ void k_power_finalize(const double *__restrict__ p64, float *__restrict__ out, int n, double inv) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = (float)(p64[k] * inv);
+}
+
+// Per-channel power: zero the FP64 accumulators, run the FFT pass, scale to a mean.
+corr_status power_pass(const FShape &f, const void *volt, double *acc64, float *power, cudaStream_t st) {
+    CORR_CUDA_TRY(cudaMemsetAsync(acc64, 0, sizeof(double) * f.n_chan, st));
+    corr_status s = dispatch<kPower>(f, volt, nullptr, nullptr, acc64, st);
+    if (s != CORR_OK) return s;
+    const double inv = 1.0 / (2.0 * (double)f.n_in * (double)f.n_spectra);
+    k_power_finalize<<<(f.n_chan + 255) / 256, 256, 0, st>>>(acc64, power, f.n_chan, inv);
+    return check_launch("k_power_finalize");
+}
+
 }  // namespace
 
 bool fengine_supported(int n) { return n == 16 || n == 64 || n == 256 || n == 1024; }
 
 corr_status launch_fengine(const Handle &h, const void *volt, const float *scale, void *out,
                            cudaStream_t st) {
-    if (h.precision == CORR_PREC_INT8) return dispatch<kRequant>(h, volt, scale, out, nullptr, st);
-    return dispatch<kFloatOut>(h, volt, nullptr, out, nullptr, st);
+    if (h.precision == CORR_PREC_INT8) return dispatch<kRequant>(shape_of(h), volt, scale, out, nullptr, st);
+    return dispatch<kFloatOut>(shape_of(h), volt, nullptr, out, nullptr, st);
 }
-
-namespace {
-__global__ void k_power_finalize(const double *__restrict__ p64, float *__restrict__ out, int n, double inv) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) out[k] = (float)(p64[k] * inv);
-}
-}  // namespace
 
 corr_status launch_fengine_power(const Handle &h, const void *volt, float *power, cudaStream_t st) {
-    CORR_CUDA_TRY(cudaMemsetAsync(h.power64, 0, sizeof(double) * h.n_chan, st));
-    corr_status s = dispatch<kPower>(h, volt, nullptr, nullptr, h.power64, st);
-    if (s != CORR_OK) return s;
-    const double inv = 1.0 / (2.0 * (double)h.n_in * (double)h.n_spectra);
-    k_power_finalize<<<(h.n_chan + 255) / 256, 256, 0, st>>>(h.power64, power, h.n_chan, inv);
-    return check_launch("k_power_finalize");
+    return power_pass(shape_of(h), volt, h.power64, power, st);
 }
 
 }  // namespace corr
