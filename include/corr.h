@@ -116,6 +116,28 @@ CORR_API corr_status corr_fengine(corr_t *h, const void *volt, const float *chan
  *   volt as for corr_fengine; power [n_chan] float (device), overwritten. */
 CORR_API corr_status corr_fengine_power(corr_t *h, const void *volt, float *power, void *stream);
 
+/* The per-channel power pass of corr_fengine_power for callers that cannot
+ * allocate device memory: it takes no handle and calls no cudaMalloc, cudaFree
+ * or other allocating routine. (The paper has no counterpart; this serves hosts
+ * that own all device memory themselves, e.g. a real-time pipeline whose memory
+ * is fixed up front, or code where an allocation's implicit synchronisation
+ * would stall other streams.)
+ *   volt      [n_in][n_spectra * n_chan] raw voltages, complex int8 when
+ *             precision == CORR_PREC_INT8, complex float when CORR_PREC_FP32;
+ *             16-byte aligned, device.
+ *   power     [n_chan] float, device: sum_{i,a} |S_a,i[k]|^2 / (2 n_in n_spectra).
+ * n_chan must be one of 16, 64, 256, 1024: larger values are rejected with
+ * CORR_EINVAL (the static scratch holds 1024 FP64 accumulators), others with
+ * CORR_EUNSUPPORTED. The scratch and twiddle tables are file-scope device arrays
+ * (about 19 KB) that each GPU loading the library keeps until the process exits.
+ * The first call on a device sets them up (a synchronous host-to-device copy)
+ * and should be made before any stream capture. All calls on a device share the
+ * scratch: calls that overlap on the GPU race, so serialise them (one stream,
+ * or events). Runs on the current device and `stream`. */
+CORR_API corr_status corr_fengine_power_noalloc(const void *volt, int32_t n_in, int32_t n_chan,
+                                                int32_t n_spectra, int32_t precision, float *power,
+                                                void *stream);
+
 /* X-engine, Eq. 2 (Section 2), for one integration of n_spectra spectra: adds
  * V'_ij[k] = g_i conj(g_j) sum_a X_a,i[k] conj(X_a,j[k]) (i >= j) into the
  * library-owned integration accumulator.

@@ -47,6 +47,8 @@ SIGNATURES = [
     ("corr_check_status", _S, [_P, _P]),
     ("corr_reset", _S, [_P, _P]),
     ("corr_backward", _S, [_P, _P, _P, _P, _P, _P, _P]),
+    ("corr_fengine_power_noalloc", _S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        _P, _P]),
 ]
 
 _lib = None

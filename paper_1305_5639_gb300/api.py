@@ -66,6 +66,14 @@ def corr_fengine_power(h, volt, power, stream=None) -> None:
     check(_lib.load().corr_fengine_power(h, _ptr(volt), _ptr(power), _stream(stream)), "corr_fengine_power")
 
 
+def corr_fengine_power_noalloc(volt, n_in: int, n_chan: int, n_spectra: int, precision, power,
+                               stream=None) -> None:
+    """Per-channel power pass that allocates no device memory (no handle)."""
+    prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    check(_lib.load().corr_fengine_power_noalloc(_ptr(volt), n_in, n_chan, n_spectra, prec, _ptr(power),
+                                                 _stream(stream)), "corr_fengine_power_noalloc")
+
+
 def corr_xengine(h, chan_in, gains=None, stream=None) -> None:
     check(_lib.load().corr_xengine(h, _ptr(chan_in), _ptr(gains), _stream(stream)), "corr_xengine")
 

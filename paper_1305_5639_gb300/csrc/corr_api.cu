@@ -17,6 +17,8 @@ void set_cuda_error(cudaError_t e, const char *what) {
                   cudaGetErrorString(e));
 }
 
+void set_error_text(const char *text) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", text); }
+
 corr_status check_launch(const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

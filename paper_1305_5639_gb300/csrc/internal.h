@@ -29,6 +29,7 @@ struct Handle {
 
 // Error bookkeeping (per thread).
 void set_cuda_error(cudaError_t e, const char *what);
+void set_error_text(const char *text);
 corr_status check_launch(const char *what);
 
 #define CORR_CUDA_TRY(expr)                                  \
