@@ -67,10 +67,19 @@ enum {
  * and CUDA cores for FP32. CUDACORE with INT8 uses exact dp4a integer arithmetic. */
 enum { CORR_XENG_AUTO = 0, CORR_XENG_CUDACORE = 1, CORR_XENG_TCGEN05 = 2 };
 
+/* Layout flags (corr_opts.flags).
+ * CORR_FLAG_PLANAR (INT8 only): channelised data is exchanged in the planar FP16
+ *   layout [n_chan][2][n_in][n_spectra] (plane 0 = Re, plane 1 = Im; 2 bytes per
+ *   component) instead of complex int8. The values are the same int8 codes, held
+ *   exactly in FP16, so results are unchanged; the X-engine then streams its
+ *   operands straight into shared memory with TMA. Requires n_spectra % 8 == 0
+ *   (CORR_EUNSUPPORTED otherwise); doubles the channelised buffer's size. */
+enum { CORR_FLAG_PLANAR = 1 };
+
 typedef struct corr_opts {
     int32_t precision; /* CORR_PREC_*, default CORR_PREC_FP32 */
     int32_t xengine;   /* CORR_XENG_*, default CORR_XENG_AUTO */
-    int32_t flags;     /* reserved, must be 0 */
+    int32_t flags;     /* CORR_FLAG_* bits, default 0 */
     int32_t device;    /* CUDA device ordinal; -1 = the current device */
 } corr_opts;
 
@@ -106,7 +115,8 @@ CORR_API int64_t corr_n_baselines(const corr_t *h);
  *             expanded spectra, Section 6.2).
  *   chan_out  [n_chan][n_in][n_spectra] channel-major ("corner-turned") output:
  *             complex int8 for INT8, complex float (FP32 FFT, unnormalised)
- *             otherwise. 16-byte aligned. */
+ *             otherwise; with CORR_FLAG_PLANAR the planar FP16 layout
+ *             [n_chan][2][n_in][n_spectra]. 16-byte aligned. */
 CORR_API corr_status corr_fengine(corr_t *h, const void *volt, const float *chan_scale, void *chan_out,
                          void *stream);
 
@@ -142,7 +152,8 @@ CORR_API corr_status corr_fengine_power_noalloc(const void *volt, int32_t n_in, 
  * V'_ij[k] = g_i conj(g_j) sum_a X_a,i[k] conj(X_a,j[k]) (i >= j) into the
  * library-owned integration accumulator.
  *   chan_in [n_chan][n_in][n_spectra]: complex int8 for INT8, complex float
- *           otherwise (FP16 paths round or split it on the fly). 16-byte aligned.
+ *           otherwise (FP16 paths round or split it on the fly); with
+ *           CORR_FLAG_PLANAR the planar FP16 layout. 16-byte aligned.
  *   gains   [n_in] complex float, or NULL for unit gains. Not allowed with INT8
  *           (the INT8 result is an exact integer; CORR_EINVAL).
  * INT8: accumulator is INT32 per component; CORR_EOVERFLOW if the spectra

@@ -40,10 +40,10 @@ def _stream(stream):
 
 
 def corr_create(n_ant: int, n_pol: int, n_chan: int, n_spectra: int, precision="fp32", xengine="auto",
-                device: int = -1) -> ctypes.c_void_p:
+                device: int = -1, flags: int = 0) -> ctypes.c_void_p:
     lib = _lib.load()
     o = corr_opts(PREC[precision] if isinstance(precision, str) else int(precision),
-                  XENG[xengine] if isinstance(xengine, str) else int(xengine), 0, int(device))
+                  XENG[xengine] if isinstance(xengine, str) else int(xengine), int(flags), int(device))
     h = ctypes.c_void_p()
     check(lib.corr_create(n_ant, n_pol, n_chan, n_spectra, ctypes.byref(o), ctypes.byref(h)), "corr_create")
     return h
@@ -103,14 +103,16 @@ class Correlator:
     """Owns one libcorr handle; allocates outputs as torch tensors."""
 
     def __init__(self, n_ant: int, n_pol: int, n_chan: int, n_spectra: int, precision="fp32", xengine="auto",
-                 device=None):
+                 device=None, planar: bool = False):
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else int(device))
         self.device = dev
         self.n_ant, self.n_pol, self.n_chan, self.n_spectra = n_ant, n_pol, n_chan, n_spectra
         self.n_in = n_ant * n_pol
         self.precision = precision
+        self.planar = planar
         with torch.cuda.device(dev):
-            self.h = corr_create(n_ant, n_pol, n_chan, n_spectra, precision, xengine, dev.index)
+            self.h = corr_create(n_ant, n_pol, n_chan, n_spectra, precision, xengine, dev.index,
+                                 _lib.CORR_FLAG_PLANAR if planar else 0)
         self.n_base = corr_n_baselines(self.h)
 
     def close(self):
@@ -126,6 +128,8 @@ class Correlator:
 
     # -- buffers
     def chan_buffer(self):
+        if self.planar:
+            return torch.empty((self.n_chan, 2, self.n_in, self.n_spectra), dtype=torch.float16, device=self.device)
         if self.precision == "int8":
             return torch.empty((self.n_chan, self.n_in, self.n_spectra, 2), dtype=torch.int8, device=self.device)
         return torch.empty((self.n_chan, self.n_in, self.n_spectra), dtype=torch.complex64, device=self.device)

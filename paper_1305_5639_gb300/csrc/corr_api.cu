@@ -107,7 +107,10 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
     if (opts) o = *opts;
     if (o.precision < CORR_PREC_FP32 || o.precision > CORR_PREC_FP16_HILO) return CORR_EINVAL;
     if (o.xengine < CORR_XENG_AUTO || o.xengine > CORR_XENG_TCGEN05) return CORR_EINVAL;
-    if (o.flags != 0) return CORR_EINVAL;
+    if ((o.flags & ~CORR_FLAG_PLANAR) != 0) return CORR_EINVAL;
+    if ((o.flags & CORR_FLAG_PLANAR) &&
+        (o.precision != CORR_PREC_INT8 || o.xengine == CORR_XENG_CUDACORE || (n_spectra % 8) != 0))
+        return CORR_EUNSUPPORTED;
     if (o.precision == CORR_PREC_INT8) {
         // INT32 guard: |Re V| <= n_spectra * 2 * 127^2 must stay below 2^31
         if ((int64_t)n_spectra * 2 * 127 * 127 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
@@ -126,6 +129,7 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
     h.n_base = n_in * (n_in + 1) / 2;
     h.precision = o.precision;
     h.xengine = o.xengine;
+    h.flags = o.flags;
     if (o.device >= 0) {
         h.device = o.device;
     } else if (cudaGetDevice(&h.device) != cudaSuccess) {
@@ -226,8 +230,13 @@ corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, voi
     corr::DeviceGuard dg(h.device);
     const bool store = h.acc_zero;
     const float2 *g = reinterpret_cast<const float2 *>(gains);
-    corr_status s = corr::use_tc(h) ? corr::launch_xengine_tc(h, chan_in, g, store, corr::as_stream(stream))
-                                    : corr::launch_xengine_cudacore(h, chan_in, g, store, corr::as_stream(stream));
+    corr_status s;
+    if (h.flags & CORR_FLAG_PLANAR)
+        s = corr::launch_xengine_tma(h, chan_in, g, store, corr::as_stream(stream));
+    else if (corr::use_tc(h))
+        s = corr::launch_xengine_tc(h, chan_in, g, store, corr::as_stream(stream));
+    else
+        s = corr::launch_xengine_cudacore(h, chan_in, g, store, corr::as_stream(stream));
     if (s == CORR_OK) {
         h.acc_zero = false;
         h.acc_spectra += h.n_spectra;

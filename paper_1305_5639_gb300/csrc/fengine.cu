@@ -17,6 +17,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "fft_common.cuh"
 #include "internal.h"
 
@@ -27,7 +29,7 @@ constexpr int kThreads = 256;
 
 constexpr int isqrt_pow4(int n) { return n <= 1 ? 1 : 2 * isqrt_pow4(n / 4); }
 
-enum Mode { kFloatOut = 0, kRequant = 1, kPower = 2 };
+enum Mode { kFloatOut = 0, kRequant = 1, kPower = 2, kRequantPlanar = 3 };
 
 template <int N, bool I8, int MODE>
 struct FCfg {
@@ -36,13 +38,16 @@ struct FCfg {
     static constexpr int G = kThreads / T;  // FFTs in flight per CTA
     static constexpr int EXS = T + 1;       // exchange row stride (floats; Re and Im exchanged in turn)
     // spectra per CTA
-    static constexpr int SB = MODE == kRequant ? 16 : (MODE == kFloatOut ? 8 : 16);
+    static constexpr int SB = MODE == kFloatOut ? 8 : 16;
     static_assert(SB % (G < SB ? G : SB) == 0 || G >= SB, "");
     // staging row stride in 32-bit words
-    static constexpr int ROWW = MODE == kRequant ? SB / 2 + 1 : (MODE == kFloatOut ? 2 * SB + 2 : 0);
+    // (kRequantPlanar: two planes of N rows, each row SB fp16 codes)
+    static constexpr int ROWW = (MODE == kRequant || MODE == kRequantPlanar) ? SB / 2 + 1
+                                : (MODE == kFloatOut ? 2 * SB + 2 : 0);
+    static constexpr int NPL = MODE == kRequantPlanar ? 2 : 1;
     static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * T * EXS;
     static constexpr size_t pw_bytes = MODE == kPower ? sizeof(float) * N : 0;
-    static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW;
+    static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW * NPL;
     static constexpr size_t smem = ex_bytes + pw_bytes + st_bytes;
 };
 
@@ -58,6 +63,19 @@ __device__ __forceinline__ uint32_t pack_q(float2 v, float sc) {
     return __byte_perm(__float_as_uint(re), __float_as_uint(im), 0x0040);
 }
 
+// Same decision as pack_q, but the two int8 codes returned as FP16 values
+// (exact for |q| <= 127): low 16 bits Re, high 16 bits Im.
+__device__ __forceinline__ uint32_t pack_q_f16(float2 v, float sc) {
+    const float re = fminf(fmaxf(v.x * sc, -127.0f), 127.0f) + kMagic;
+    const float im = fminf(fmaxf(v.y * sc, -127.0f), 127.0f) + kMagic;
+    // [q_re + 128, q_im + 128] in the low bytes, then the half 1024 + u, minus 1152
+    const uint32_t u = __byte_perm(__float_as_uint(re), __float_as_uint(im), 0x0040) ^ 0x8080u;
+    uint32_t h = __byte_perm(u, 0x64646464u, 0x5140);
+    __half2 hv = *reinterpret_cast<__half2 *>(&h);
+    hv = __hsub2(hv, __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)));
+    return *reinterpret_cast<uint32_t *>(&hv);
+}
+
 // complex int8 sample (16 bits: re in the low byte) -> float2, exactly:
 // (0x4B400000 | (x + 128)) is the float 12582912 + x + 128.
 __device__ __forceinline__ float2 i8_to_f2(uint32_t w) {
@@ -67,7 +85,7 @@ __device__ __forceinline__ float2 i8_to_f2(uint32_t w) {
 }
 
 template <int N, bool I8, int MODE>
-__global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 : 3) k_fengine(const void *__restrict__ volt,
+__global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant && MODE != kRequantPlanar) ? 2 : 3) k_fengine(const void *__restrict__ volt,
                                                       const float *__restrict__ scale,
                                                       void *__restrict__ out,
                                                       double *__restrict__ power, int n_in, int K,
@@ -147,6 +165,11 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
                 if constexpr (MODE == kRequant) {
                     uint32_t q = pack_q(x, __ldg(scale + k));
                     reinterpret_cast<uint16_t *>(stg)[(size_t)k * (2 * ROWW) + s] = (uint16_t)q;
+                } else if constexpr (MODE == kRequantPlanar) {
+                    const uint32_t q = pack_q_f16(x, __ldg(scale + k));
+                    uint16_t *sh = reinterpret_cast<uint16_t *>(stg);
+                    sh[(size_t)k * (2 * ROWW) + s] = (uint16_t)(q & 0xffffu);
+                    sh[(size_t)(N + k) * (2 * ROWW) + s] = (uint16_t)(q >> 16);
                 } else if constexpr (MODE == kFloatOut) {
                     reinterpret_cast<float2 *>(stg)[(size_t)k * (ROWW / 2) + s] = x;
                 } else {
@@ -168,7 +191,26 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
         __syncthreads();
         // ---- corner turn: row (k, i) gets spectra a0 .. a0 + nv - 1
         const int nv = min(SB, K - a0);
-        if constexpr (MODE == kRequant) {
+        if constexpr (MODE == kRequantPlanar) {
+            // planar FP16 layout [k][plane][i][a]: plane p row of channel k
+            uint16_t *dst = reinterpret_cast<uint16_t *>(out);
+            const uint16_t *sh = reinterpret_cast<const uint16_t *>(stg);
+            if (nv == SB && (K % 2) == 0) {
+                constexpr int WPR = SB / 2;
+                for (int w = threadIdx.x; w < 2 * N * WPR; w += kThreads) {
+                    const int row = w / WPR, c = w % WPR;  // row = p * N + k
+                    const int pl = row / N, k = row % N;
+                    uint32_t *d = reinterpret_cast<uint32_t *>(dst + (((size_t)k * 2 + pl) * n_in + i) * K + a0);
+                    d[c] = stg[(size_t)row * ROWW + c];
+                }
+            } else {
+                for (int e = threadIdx.x; e < 2 * N * SB; e += kThreads) {
+                    const int row = e / SB, c = e % SB;
+                    const int pl = row / N, k = row % N;
+                    if (c < nv) dst[(((size_t)k * 2 + pl) * n_in + i) * K + a0 + c] = sh[(size_t)row * (2 * ROWW) + c];
+                }
+            }
+        } else if constexpr (MODE == kRequant) {
             uint16_t *dst = reinterpret_cast<uint16_t *>(out);
             const uint16_t *sh = reinterpret_cast<const uint16_t *>(stg);
             if (nv == SB && (K % 2) == 0) {
@@ -256,6 +298,8 @@ bool fengine_supported(int n) { return n == 16 || n == 64 || n == 256 || n == 10
 
 corr_status launch_fengine(const Handle &h, const void *volt, const float *scale, void *out,
                            cudaStream_t st) {
+    if (h.precision == CORR_PREC_INT8 && (h.flags & CORR_FLAG_PLANAR))
+        return dispatch<kRequantPlanar>(shape_of(h), volt, scale, out, nullptr, st);
     if (h.precision == CORR_PREC_INT8) return dispatch<kRequant>(shape_of(h), volt, scale, out, nullptr, st);
     return dispatch<kFloatOut>(shape_of(h), volt, nullptr, out, nullptr, st);
 }

@@ -12,7 +12,7 @@ namespace corr {
 struct Handle {
     int32_t n_ant, n_pol, n_in, n_chan, n_spectra;
     int64_t n_base;  // B = n_in (n_in + 1) / 2
-    int32_t precision, xengine;
+    int32_t precision, xengine, flags;
     int32_t device;
     int32_t n_sm;
     // integration accumulator [n_chan][B]: int2 (INT8) or float2 (float paths)
@@ -55,6 +55,9 @@ corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const fl
                                const float2 *gains, float2 *grad_chan, float2 *grad_gains, float2 *ws,
                                cudaStream_t st);
 bool fengine_supported(int n_chan);
+bool xengine_tma_supported(const Handle &h);
+corr_status launch_xengine_tma(const Handle &h, const void *planes, const float2 *gains, bool store,
+                               cudaStream_t st);
 
 // Bounded-wait iteration limit for device-side spins (mbarrier waits).
 constexpr long long kSpinLimit = 1LL << 26;

@@ -1,0 +1,373 @@
+// X-engine on tcgen05 tensor cores fed by TMA from the planar FP16 layout
+// X[f][plane][input][spectrum] (plane 0 = Re, 1 = Im), Eq. 2 of Section 2 as a
+// Hermitian rank-K update V[f] += X[f] X[f]^H over the lower triangle.
+//
+// For a tile of 128 inputs I (rows) x 128 inputs J, four real MMAs of M = 128,
+// N = 128, K = 16 per 16 spectra accumulate
+//     D[:, 0:128]   += re_I re_J^T + im_I im_J^T   = Re V_IJ
+//     D[:, 128:256] += im_I re_J^T - re_I im_J^T   = Im V_IJ
+// the minus sign coming from the instruction descriptor's negate-A bit, so only
+// the Re and Im planes are stored. Diagonal tiles (I == J) load the J planes once.
+//
+// INT8 codes (|x| <= 127) are exact in FP16 and their products exact in FP32;
+// each accumulator column sums at most 2 * 127^2 * 512 < 2^24, so an FP32
+// partial over <= 512 spectra is an exact integer. The accumulator is double
+// buffered in TMEM (2 x 256 columns): while the MMAs fill one buffer with the next
+// 512 spectra, the epilogue converts the other exactly and adds it into INT32
+// running sums held in registers. The result is bit-exact.
+//
+// Warp roles (384 threads, one persistent CTA per SM):
+//   warp 0       TMA producer (one thread): 3-stage ring of 64-spectrum stages
+//   warp 1       TMEM allocator + single-thread MMA issuer
+//   warps 4-11   epilogue, two warps per TMEM lane quarter, each owning half of
+//                the tile's columns and their INT32 sums
+// Every mbarrier wait is bounded; on time-out the CTA records CORR_ETIMEOUT and
+// every role leaves its loop.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace corr {
+namespace {
+
+constexpr int TILE = 128;
+constexpr int KB = 64;                    // spectra per stage: 128 B of FP16 per row
+constexpr int PLANE = TILE * KB * 2;      // 16 KB per plane block
+constexpr int STAGE_BYTES = 4 * PLANE;    // A_re, A_im, B_re, B_im
+constexpr int NSTAGE = 3;
+constexpr int CHUNK_KB = 8;               // INT8: fold every 512 spectra
+constexpr int NEPI = 256;                 // epilogue threads (warps 4..11)
+constexpr int NTHREADS = 384;
+constexpr int OFF_ARE = 0, OFF_AIM = PLANE, OFF_BRE = 2 * PLANE, OFF_BIM = 3 * PLANE;
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
+
+enum Mode { kInt8 = 0, kFp16 = 1 };
+
+struct TParams {
+    void *acc;
+    const float2 *gains;
+    int *status;
+    long long B;
+    long long n_items;
+    int n_in, K, n_tiles, store;
+};
+
+__device__ __forceinline__ void decode(long long item, int n_tiles, int &chan, int &bi, int &bj) {
+    chan = (int)(item / n_tiles);
+    int t = (int)(item % n_tiles);
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    bi = r;
+    bj = t - r * (r + 1) / 2;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant__ CUtensorMap tmap, const TParams p) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    unsigned char *sgen = smem_raw + (sbase - raw);
+    const uint32_t bar0 = sbase + NSTAGE * STAGE_BYTES;
+    // barriers: full[NSTAGE], empty[NSTAGE], accf[2], acce[2], drain; then tmem slot, abort flag
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (NSTAGE + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * NSTAGE + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * NSTAGE + 2 + b); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * NSTAGE + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sgen + NSTAGE * STAGE_BYTES + 8 * (2 * NSTAGE + 5));
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            tc::mbar_init(full_bar(s), 1);
+            tc::mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(accf_bar(b), 1);
+            tc::mbar_init(acce_bar(b), NEPI);
+        }
+        tc::mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tc::prefetch_tmap(&tmap);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tc::smem_u32(tmem_slot), 512);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nkb = (p.K + KB - 1) / KB;
+    const long long my_items = (p.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    // accumulator hand-offs: INT8 one per 512-spectrum chunk, FP16 one per tile
+    const int chunks_per_item = MODE == kInt8 ? (nkb + CHUNK_KB - 1) / CHUNK_KB : 1;
+    const int chunk_kb = MODE == kInt8 ? CHUNK_KB : nkb;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            long long n = 0;
+            for (long long it = 0; it < my_items; ++it) {
+                int chan, bi, bj;
+                decode(blockIdx.x + it * gridDim.x, p.n_tiles, chan, bi, bj);
+                const bool diag = bi == bj;
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++n) {
+                    const int slot = (int)(n % NSTAGE);
+                    if (!tc::mbar_wait(empty_bar(slot), (uint32_t)(((n / NSTAGE) & 1) ^ 1), abort_flag, p.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = sbase + slot * STAGE_BYTES;
+                    tc::mbar_arrive_expect_tx(full_bar(slot), diag ? 2 * PLANE : 4 * PLANE);
+                    const int s0 = kb * KB;
+                    tc::tma_load_4d(st + OFF_BRE, &tmap, s0, bj * TILE, 0, chan, full_bar(slot));
+                    tc::tma_load_4d(st + OFF_BIM, &tmap, s0, bj * TILE, 1, chan, full_bar(slot));
+                    if (!diag) {
+                        tc::tma_load_4d(st + OFF_ARE, &tmap, s0, bi * TILE, 0, chan, full_bar(slot));
+                        tc::tma_load_4d(st + OFF_AIM, &tmap, s0, bi * TILE, 1, chan, full_bar(slot));
+                    }
+                }
+                if (!ok) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t ID = tc::idesc_f16(128, 128);
+            constexpr uint32_t ID_NEG = tc::idesc_f16(128, 128, /*neg_a=*/true);
+            uint32_t ae_phase[2] = {0, 0};
+            long long n = 0, ch = 0;  // stage and accumulator-chunk counters
+            bool alive = true;
+            for (long long it = 0; it < my_items && alive; ++it) {
+                int chan, bi, bj;
+                decode(blockIdx.x + it * gridDim.x, p.n_tiles, chan, bi, bj);
+                const bool diag = bi == bj;
+                uint32_t d_re = 0, d_im = 0;
+                int buf = 0;
+                for (int kb = 0; kb < nkb; ++kb, ++n) {
+                    const int kin = kb % chunk_kb;
+                    if (kin == 0) {
+                        buf = (int)(ch & 1);
+                        if (!tc::mbar_wait(acce_bar(buf), ae_phase[buf] ^ 1u, abort_flag, p.status)) {
+                            alive = false;
+                            break;
+                        }
+                        ae_phase[buf] ^= 1u;
+                        tc::tc_fence_after();
+                        d_re = tmem + (uint32_t)(buf * 256);
+                        d_im = d_re + 128u;
+                    }
+                    const int slot = (int)(n % NSTAGE);
+                    if (!tc::mbar_wait(full_bar(slot), (uint32_t)((n / NSTAGE) & 1), abort_flag, p.status)) {
+                        alive = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t st = sbase + slot * STAGE_BYTES;
+                    const uint32_t a_re = st + (diag ? OFF_BRE : OFF_ARE);
+                    const uint32_t a_im = st + (diag ? OFF_BIM : OFF_AIM);
+#pragma unroll
+                    for (int k = 0; k < KB / 16; ++k) {
+                        const uint32_t ko = 32u * k;
+                        const uint32_t acc = (kin > 0 || k > 0) ? 1u : 0u;
+                        const uint64_t dre = tc::desc_sw128(a_re + ko), dim = tc::desc_sw128(a_im + ko);
+                        const uint64_t bre = tc::desc_sw128(st + OFF_BRE + ko), bim = tc::desc_sw128(st + OFF_BIM + ko);
+                        tc::mma_f16(d_re, dre, bre, ID, acc);
+                        tc::mma_f16(d_re, dim, bim, ID, 1u);
+                        tc::mma_f16(d_im, dim, bre, ID, acc);
+                        tc::mma_f16(d_im, dre, bim, ID_NEG, 1u);
+                    }
+                    tc::mma_commit(empty_bar(slot));
+                    if (kin == chunk_kb - 1 || kb == nkb - 1) {
+                        tc::mma_commit(accf_bar(buf));
+                        ++ch;
+                    }
+                }
+            }
+            tc::mma_commit(drain_bar);
+            tc::mbar_wait(drain_bar, 0u, abort_flag, p.status, 1000000000ull, false);
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ------------------------------------------------------------ epilogue
+        const int ew = warp - 4;               // 0..7
+        const int wq = warp & 3;               // TMEM lane quarter this warp may access
+        const int h = ew >> 2;                 // column half: j in [64 h, 64 h + 64)
+        const int m = wq * 32 + lane;          // tile row = TMEM lane
+        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+        uint32_t af_phase[2] = {0, 0};
+        long long ch = 0;
+        bool alive = true;
+        for (long long it = 0; it < my_items && alive; ++it) {
+            int chan, bi, bj;
+            decode(blockIdx.x + it * gridDim.x, p.n_tiles, chan, bi, bj);
+            const int I0 = bi * TILE, J0 = bj * TILE;
+            const int i = I0 + m;
+            if constexpr (MODE == kInt8) {
+                int R[128];  // INT32 sums: Re of j = J0 + 64h + x in R[x], Im in R[64 + x]
+#pragma unroll
+                for (int x = 0; x < 128; ++x) R[x] = 0;
+                for (int c = 0; c < chunks_per_item; ++c, ++ch) {
+                    const int buf = (int)(ch & 1);
+                    if (!tc::mbar_wait(accf_bar(buf), af_phase[buf], abort_flag, p.status)) {
+                        alive = false;
+                        break;
+                    }
+                    af_phase[buf] ^= 1u;
+                    tc::tc_fence_after();
+                    const uint32_t d = tmem + lane_off + (uint32_t)(buf * 256) + (uint32_t)(64 * h);
+#pragma unroll
+                    for (int cb = 0; cb < 8; ++cb) {
+                        // cb < 4: Re columns 64h + 16 cb; cb >= 4: Im columns 128 + 64h + 16 (cb - 4)
+                        uint32_t v[16];
+                        tc::tmem_ld16(d + (cb < 4 ? 0u : 128u) + 16u * (cb & 3), v);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int x = 0; x < 16; ++x) R[16 * cb + x] += __float2int_rn(__uint_as_float(v[x]));
+                    }
+                    tc::tc_fence_before();
+                    tc::mbar_arrive(acce_bar(buf));
+                }
+                if (!alive) break;
+                if (i < p.n_in) {
+                    int2 *row = static_cast<int2 *>(p.acc) + (size_t)chan * p.B + (size_t)i * (i + 1) / 2;
+#pragma unroll
+                    for (int x = 0; x < 64; ++x) {
+                        const int j = J0 + 64 * h + x;
+                        if (j <= i) {
+                            int2 o = make_int2(R[x], R[64 + x]);
+                            if (!p.store) {
+                                const int2 q = row[j];
+                                o.x += q.x;
+                                o.y += q.y;
+                            }
+                            row[j] = o;
+                        }
+                    }
+                }
+            } else {
+                const int buf = (int)(ch & 1);
+                if (!tc::mbar_wait(accf_bar(buf), af_phase[buf], abort_flag, p.status)) break;
+                af_phase[buf] ^= 1u;
+                tc::tc_fence_after();
+                const uint32_t d = tmem + lane_off + (uint32_t)(buf * 256) + (uint32_t)(64 * h);
+                float2 gi = make_float2(1.f, 0.f);
+                if (p.gains && i < p.n_in) gi = __ldg(p.gains + i);
+                float2 *row = static_cast<float2 *>(p.acc) + (size_t)chan * p.B + (size_t)i * (i + 1) / 2;
+#pragma unroll 1
+                for (int cb = 0; cb < 4; ++cb) {
+                    uint32_t re[16], im[16];
+                    tc::tmem_ld16(d + 16u * cb, re);
+                    tc::tmem_ld16(d + 128u + 16u * cb, im);
+                    tc::tmem_wait_ld();
+                    if (i < p.n_in) {
+#pragma unroll
+                        for (int x = 0; x < 16; ++x) {
+                            const int j = J0 + 64 * h + 16 * cb + x;
+                            if (j <= i) {
+                                float2 v = make_float2(__uint_as_float(re[x]), __uint_as_float(im[x]));
+                                if (p.gains) {
+                                    const float2 gj = __ldg(p.gains + j);
+                                    const float2 w = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
+                                    v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+                                }
+                                if (!p.store) {
+                                    const float2 o = row[j];
+                                    v.x += o.x;
+                                    v.y += o.y;
+                                }
+                                row[j] = v;
+                            }
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+                tc::mbar_arrive(acce_bar(buf));
+                ++ch;
+            }
+        }
+    }
+
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------------ tensor map
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+
+}  // namespace
+
+bool xengine_tma_supported(const Handle &h) { return (h.n_spectra % 8) == 0 && encode_fn() != nullptr; }
+
+corr_status launch_xengine_tma(const Handle &h, const void *planes, const float2 *gains, bool store,
+                               cudaStream_t st) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        set_error_text("cuTensorMapEncodeTiled is not available from the driver");
+        return CORR_EUNSUPPORTED;
+    }
+    if ((h.n_spectra % 8) != 0) return CORR_EUNSUPPORTED;
+    // planar FP16 tensor: dims (innermost first) spectrum, input, plane, channel
+    CUtensorMap tmap;
+    const cuuint64_t dims[4] = {(cuuint64_t)h.n_spectra, (cuuint64_t)h.n_in, 2, (cuuint64_t)h.n_chan};
+    const cuuint64_t strides[3] = {(cuuint64_t)h.n_spectra * 2, (cuuint64_t)h.n_spectra * 2 * h.n_in,
+                                   (cuuint64_t)h.n_spectra * 2 * h.n_in * 2};
+    const cuuint32_t box[4] = {KB, TILE, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(planes), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error_text("cuTensorMapEncodeTiled rejected the planar layout");
+        return CORR_EINVAL;
+    }
+    TParams p;
+    p.acc = h.acc;
+    p.gains = gains;
+    p.status = h.status;
+    p.B = h.n_base;
+    const int nb = (h.n_in + TILE - 1) / TILE;
+    p.n_tiles = nb * (nb + 1) / 2;
+    p.n_items = (long long)h.n_chan * p.n_tiles;
+    p.n_in = h.n_in;
+    p.K = h.n_spectra;
+    p.store = store ? 1 : 0;
+    const long long grid = p.n_items < h.n_sm ? p.n_items : h.n_sm;
+    if (h.precision == CORR_PREC_INT8) {
+        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        k_xeng_tma<kInt8><<<(unsigned)grid, NTHREADS, SMEM_BYTES, st>>>(tmap, p);
+    } else {
+        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        k_xeng_tma<kFp16><<<(unsigned)grid, NTHREADS, SMEM_BYTES, st>>>(tmap, p);
+    }
+    return check_launch("k_xeng_tma");
+}
+
+}  // namespace corr

@@ -104,3 +104,81 @@ def test_tc_fp16_gains(cuda_ok):
     emax, _ = norm_err(V, ref, n_in)
     assert emax <= 2e-3
     c.close()
+
+
+# --------------------------------------------------------------------------- planar FP16 layout + TMA X-engine
+def to_planar(X):
+    """complex int8 [n_chan, n_in, K, 2] -> planar FP16 [n_chan, 2, n_in, K] (same integer values)."""
+    return np.ascontiguousarray(np.transpose(X, (0, 3, 1, 2)).astype(np.float16))
+
+
+@pytest.mark.parametrize("n_in,K,n_chan", [
+    (128, 64, 1),      # one diagonal tile, one stage
+    (256, 640, 2),     # 3 tiles, two 512-spectrum folds on alternating accumulators
+    (200, 104, 3),     # ragged inputs and a partial stage (TMA zero fill)
+    (130, 1032, 1),    # 2 x 2 blocks, 3 folds
+    (1, 8, 2),         # a single input
+    (512, 4096, 2),    # the INT8 workload's channel shape
+])
+def test_tma_planar_int8_bit_exact(cuda_ok, n_in, K, n_chan):
+    X = synth.chan_int8(n_chan, n_in, K, seed=n_in + 7 * K)
+    c = api.Correlator(n_in, 1, n_chan, K, precision="int8", planar=True)
+    c.xengine(torch.from_numpy(to_planar(X)).to(DEV))
+    V = c.accum().cpu().numpy().astype(np.int64)
+    c.check_status()
+    assert np.array_equal(V, oracle.cmac(X))
+    c.close()
+
+
+def test_tma_planar_extreme_values_and_accumulate(cuda_ok):
+    n_in, K = 160, 4096
+    rng = np.random.default_rng(1)
+    X = np.where(rng.random((1, n_in, K, 2)) < 0.5, 127, -127).astype(np.int8)
+    X[0, :8] = 127
+    c = api.Correlator(n_in, 1, 1, K, precision="int8", planar=True)
+    P = torch.from_numpy(to_planar(X)).to(DEV)
+    c.xengine(P)
+    c.xengine(P)  # accumulate a second integration (INT32 guard allows 2 x 4096)
+    V = c.accum().cpu().numpy().astype(np.int64)
+    assert np.array_equal(V, 2 * oracle.cmac(X))
+    c.close()
+
+
+def test_fengine_planar_matches_int8_layout_and_oracle(cuda_ok):
+    n_ant, n_pol, N, K = 3, 2, 1024, 40
+    v = synth.volt_int8(n_ant, n_pol, N, K, seed=9)
+    scale = np.full(N, 1.0 / 32.0, np.float32)
+    vt, st = torch.from_numpy(v).to(DEV), torch.from_numpy(scale).to(DEV)
+    a = api.Correlator(n_ant, n_pol, N, K, precision="int8")
+    b = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
+    q8 = a.fengine(vt, st).cpu().numpy()            # [N, n_in, K, 2] int8
+    qp = b.fengine(vt, st).cpu().numpy()            # [N, 2, n_in, K] float16
+    assert np.array_equal(to_planar(q8), qp)
+    S = oracle.channelise(v, N)
+    q, margin = oracle.requant(S, scale)
+    sure = margin > 1e-3
+    assert np.array_equal(q8[sure], q[sure])
+    a.close()
+    b.close()
+
+
+def test_full_fx_planar_int8_workload_shape(cuda_ok):
+    """F-engine -> planar -> TMA X-engine on a channel subset of the INT8 workload:
+    the X-engine result equals the oracle's CMAC of the GPU F-engine output read
+    back as int8 (bit-exact), and the F-engine matches the oracle's DFT."""
+    n_ant, n_pol, N, K = 16, 2, 1024, 256
+    v = synth.volt_int8(n_ant, n_pol, N, K, seed=11)
+    c = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
+    vt = torch.from_numpy(v).to(DEV)
+    scale = (16.0 / torch.sqrt(c.fengine_power(vt))).contiguous()
+    P = c.fengine(vt, scale)
+    c.xengine(P)
+    V = c.accum().cpu().numpy().astype(np.int64)
+    Xq = np.transpose(P.cpu().numpy(), (0, 2, 3, 1)).astype(np.int8)  # [N, n_in, K, 2]
+    sel = [0, 5, 511, 1023]
+    assert np.array_equal(V[sel], oracle.cmac(np.ascontiguousarray(Xq[sel])))
+    S = oracle.channelise(v, N, bins=sel)
+    q, margin = oracle.requant(S, scale.cpu().numpy()[sel])
+    sure = margin > 1e-3
+    assert np.array_equal(Xq[sel][sure], q[sure])
+    c.close()
