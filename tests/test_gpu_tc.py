@@ -163,22 +163,26 @@ def test_fengine_planar_matches_int8_layout_and_oracle(cuda_ok):
 
 
 def test_full_fx_planar_int8_workload_shape(cuda_ok):
-    """F-engine -> planar -> TMA X-engine on a channel subset of the INT8 workload:
-    the X-engine result equals the oracle's CMAC of the GPU F-engine output read
-    back as int8 (bit-exact), and the F-engine matches the oracle's DFT."""
+    """F-engine -> planar -> TMA X-engine on a channel subset of the INT8 workload's
+    shape, against the oracle's own chain (direct DFT, FP32 re-packing decision,
+    int64 CMAC). On every channel whose int8 codes are all unique (no value within
+    the FP32 FFT error of a rounding boundary) the visibilities must be identical."""
     n_ant, n_pol, N, K = 16, 2, 1024, 256
     v = synth.volt_int8(n_ant, n_pol, N, K, seed=11)
+    scale = np.full(N, 1.0 / 32.0, np.float32)  # rms 16 sqrt(N) -> 16
     c = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
-    vt = torch.from_numpy(v).to(DEV)
-    scale = (16.0 / torch.sqrt(c.fengine_power(vt))).contiguous()
-    P = c.fengine(vt, scale)
+    P = c.fengine(torch.from_numpy(v).to(DEV), torch.from_numpy(scale).to(DEV))
     c.xengine(P)
     V = c.accum().cpu().numpy().astype(np.int64)
-    Xq = np.transpose(P.cpu().numpy(), (0, 2, 3, 1)).astype(np.int8)  # [N, n_in, K, 2]
-    sel = [0, 5, 511, 1023]
-    assert np.array_equal(V[sel], oracle.cmac(np.ascontiguousarray(Xq[sel])))
+    sel = [0, 1, 5, 100, 511, 512, 777, 1023]
     S = oracle.channelise(v, N, bins=sel)
-    q, margin = oracle.requant(S, scale.cpu().numpy()[sel])
-    sure = margin > 1e-3
-    assert np.array_equal(Xq[sel][sure], q[sure])
+    q, margin = oracle.requant(S, scale[sel])
+    Vref = oracle.cmac(q)
+    eps = 1e-3
+    checked = 0
+    for t, k in enumerate(sel):
+        if np.all(margin[t] > eps):
+            assert np.array_equal(V[k], Vref[t]), k
+            checked += 1
+    assert checked >= 4
     c.close()
