@@ -194,7 +194,8 @@ def run_ours(args):
     volt_h = synth.volt_int8(n_ant, n_pol, N, K, seed=rank)
     volt_pin = torch.from_numpy(volt_h).pin_memory()
     volt = volt_pin.to(dev, non_blocking=False)
-    corr = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine=args.xengine)
+    planar = args.layout == "planar"
+    corr = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine=args.xengine, planar=planar)
     chan = corr.chan_buffer()
     # requantisation scale from a calibration pass: 16 / per-component RMS of each channel
     power = corr.fengine_power(volt)
@@ -277,11 +278,13 @@ def run_ours(args):
     cc_ms = None
     if args.comparator:
         cc = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine="cudacore")
-        cc.xengine(chan)
+        chan8 = cc.chan_buffer()
+        cc.fengine(volt, scale, chan8)
+        cc.xengine(chan8)
         torch.cuda.synchronize()
         a, b = ev(), ev()
         a.record(stream)
-        cc.xengine(chan)
+        cc.xengine(chan8)
         b.record(stream)
         torch.cuda.synchronize()
         cc_ms = a.elapsed_time(b)
@@ -294,7 +297,8 @@ def run_ours(args):
 
     peaks = _peaks()
     x_flops = 8.0 * cmac_step
-    f_bytes = 2.0 * n_in * N * K * 2  # read + write complex int8
+    # read complex int8 voltages + write the channelised data (2 B/complex int8, 4 B planar FP16)
+    f_bytes = float(n_in * N * K * 2 + chan.numel() * chan.element_size())
     tensor = corr_uses_tc(args.xengine)
     x_ach = x_flops / (x_ms * 1e-3) / 1e12
     if tensor:
@@ -315,6 +319,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8", "data": "synthetic",
         "config": {"workload": _workload_name(args.workload), "l2": "inputs larger than L2 (4.29 GB per step)",
+                   "layout": args.layout,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "stages_ms": {"fengine": f_ms, "xengine": x_ms, "dump": d_ms},
         "xengine_cmac_per_s": cmac_step / (x_ms * 1e-3),
@@ -351,6 +356,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="B", choices=sorted(WORKLOADS))
     ap.add_argument("--xengine", default="auto", choices=["auto", "cudacore", "tcgen05"])
+    ap.add_argument("--layout", default="planar", choices=["planar", "int8"],
+                    help="channelised layout between the engines: planar FP16 codes (TMA X-engine) or complex int8")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--comparator", type=int, default=1, help="time the CUDA-core X-engine once")
     args = ap.parse_args()
