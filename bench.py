@@ -30,6 +30,8 @@ WORKLOADS = {
     "small": (64, 2, 256, 1024),
     # same per-channel shape as B with a quarter of the channels: for ncu captures
     "prof": (256, 2, 256, 4096),
+    # B's FFT length and spectra with a quarter of the inputs: for F-engine captures
+    "prof_f": (64, 2, 1024, 4096),
 }
 METRIC = "X-engine complex-MAC/s and % tensor peak; F-engine GB/s; vs FP32 baseline at tol"
 

@@ -41,10 +41,11 @@ struct FCfg {
     static constexpr int SB = MODE == kFloatOut ? 8 : 16;
     static_assert(SB % (G < SB ? G : SB) == 0 || G >= SB, "");
     // staging row stride in 32-bit words
-    // (kRequantPlanar: two planes of N rows, each row SB fp16 codes)
+    // (both requant modes stage the int8 code pairs; the planar mode expands
+    //  them to FP16 planes while copying out)
     static constexpr int ROWW = (MODE == kRequant || MODE == kRequantPlanar) ? SB / 2 + 1
                                 : (MODE == kFloatOut ? 2 * SB + 2 : 0);
-    static constexpr int NPL = MODE == kRequantPlanar ? 2 : 1;
+    static constexpr int NPL = 1;
     static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * T * EXS;
     static constexpr size_t pw_bytes = MODE == kPower ? sizeof(float) * N : 0;
     static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW * NPL;
@@ -63,17 +64,16 @@ __device__ __forceinline__ uint32_t pack_q(float2 v, float sc) {
     return __byte_perm(__float_as_uint(re), __float_as_uint(im), 0x0040);
 }
 
-// Same decision as pack_q, but the two int8 codes returned as FP16 values
-// (exact for |q| <= 127): low 16 bits Re, high 16 bits Im.
-__device__ __forceinline__ uint32_t pack_q_f16(float2 v, float sc) {
-    const float re = fminf(fmaxf(v.x * sc, -127.0f), 127.0f) + kMagic;
-    const float im = fminf(fmaxf(v.y * sc, -127.0f), 127.0f) + kMagic;
-    // [q_re + 128, q_im + 128] in the low bytes, then the half 1024 + u, minus 1152
-    const uint32_t u = __byte_perm(__float_as_uint(re), __float_as_uint(im), 0x0040) ^ 0x8080u;
-    uint32_t h = __byte_perm(u, 0x64646464u, 0x5140);
-    __half2 hv = *reinterpret_cast<__half2 *>(&h);
-    hv = __hsub2(hv, __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)));
-    return *reinterpret_cast<uint32_t *>(&hv);
+// Two complex int8 codes [re0 im0 re1 im1] -> FP16 pairs (re0, re1) and (im0, im1),
+// exactly: the half with bits 0x64uu is 1024 + u, and u = code + 128.
+__device__ __forceinline__ void codes_to_f16_planes(uint32_t w, uint32_t &re, uint32_t &im) {
+    const uint32_t u = w ^ 0x80808080u;
+    uint32_t hr = __byte_perm(u, 0x64646464u, 0x4240), hi = __byte_perm(u, 0x64646464u, 0x4341);
+    const __half2 k1152 = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));
+    __half2 r = __hsub2(*reinterpret_cast<__half2 *>(&hr), k1152);
+    __half2 m = __hsub2(*reinterpret_cast<__half2 *>(&hi), k1152);
+    re = *reinterpret_cast<uint32_t *>(&r);
+    im = *reinterpret_cast<uint32_t *>(&m);
 }
 
 // complex int8 sample (16 bits: re in the low byte) -> float2, exactly:
@@ -162,14 +162,9 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant && MO
                 constexpr int k2 = decltype(K2)::value;
                 const int k = t + T * k2;
                 float2 x = v[bitrev(k2, ilog2(T))];
-                if constexpr (MODE == kRequant) {
+                if constexpr (MODE == kRequant || MODE == kRequantPlanar) {
                     uint32_t q = pack_q(x, __ldg(scale + k));
                     reinterpret_cast<uint16_t *>(stg)[(size_t)k * (2 * ROWW) + s] = (uint16_t)q;
-                } else if constexpr (MODE == kRequantPlanar) {
-                    const uint32_t q = pack_q_f16(x, __ldg(scale + k));
-                    uint16_t *sh = reinterpret_cast<uint16_t *>(stg);
-                    sh[(size_t)k * (2 * ROWW) + s] = (uint16_t)(q & 0xffffu);
-                    sh[(size_t)(N + k) * (2 * ROWW) + s] = (uint16_t)(q >> 16);
                 } else if constexpr (MODE == kFloatOut) {
                     reinterpret_cast<float2 *>(stg)[(size_t)k * (ROWW / 2) + s] = x;
                 } else {
@@ -192,22 +187,30 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant && MO
         // ---- corner turn: row (k, i) gets spectra a0 .. a0 + nv - 1
         const int nv = min(SB, K - a0);
         if constexpr (MODE == kRequantPlanar) {
-            // planar FP16 layout [k][plane][i][a]: plane p row of channel k
+            // planar FP16 layout [k][plane][i][a]: each staged word holds the code
+            // pairs of two spectra, expanded to one FP16 pair per plane
             uint16_t *dst = reinterpret_cast<uint16_t *>(out);
             const uint16_t *sh = reinterpret_cast<const uint16_t *>(stg);
             if (nv == SB && (K % 2) == 0) {
                 constexpr int WPR = SB / 2;
-                for (int w = threadIdx.x; w < 2 * N * WPR; w += kThreads) {
-                    const int row = w / WPR, c = w % WPR;  // row = p * N + k
-                    const int pl = row / N, k = row % N;
-                    uint32_t *d = reinterpret_cast<uint32_t *>(dst + (((size_t)k * 2 + pl) * n_in + i) * K + a0);
-                    d[c] = stg[(size_t)row * ROWW + c];
+                for (int w = threadIdx.x; w < N * WPR; w += kThreads) {
+                    const int k = w / WPR, c = w % WPR;
+                    uint32_t re, im;
+                    codes_to_f16_planes(stg[(size_t)k * ROWW + c], re, im);
+                    uint16_t *row0 = dst + (((size_t)k * 2) * n_in + i) * K + a0;
+                    reinterpret_cast<uint32_t *>(row0)[c] = re;
+                    reinterpret_cast<uint32_t *>(row0 + (size_t)n_in * K)[c] = im;
                 }
             } else {
-                for (int e = threadIdx.x; e < 2 * N * SB; e += kThreads) {
-                    const int row = e / SB, c = e % SB;
-                    const int pl = row / N, k = row % N;
-                    if (c < nv) dst[(((size_t)k * 2 + pl) * n_in + i) * K + a0 + c] = sh[(size_t)row * (2 * ROWW) + c];
+                for (int e = threadIdx.x; e < N * SB; e += kThreads) {
+                    const int k = e / SB, c = e % SB;
+                    if (c < nv) {
+                        uint32_t re, im;
+                        codes_to_f16_planes((uint32_t)sh[(size_t)k * (2 * ROWW) + c], re, im);
+                        uint16_t *row0 = dst + (((size_t)k * 2) * n_in + i) * K + a0;
+                        row0[c] = (uint16_t)(re & 0xffffu);
+                        row0[(size_t)n_in * K + c] = (uint16_t)(im & 0xffffu);
+                    }
                 }
             }
         } else if constexpr (MODE == kRequant) {
