@@ -36,6 +36,19 @@ WORKLOADS = {
 METRIC = "X-engine complex-MAC/s and % tensor peak; F-engine GB/s; vs FP32 baseline at tol"
 
 
+def _traffic(kernel):
+    """DRAM bytes per full-size launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), or None if the kernel's source changed since."""
+    import hashlib
+
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        h = hashlib.sha256(b"".join(open(os.path.join(ROOT, f), "rb").read() for f in t["files"])).hexdigest()[:16]
+        return float(t["traffic_bytes"]) if h == t["source_sha256_16"] else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -302,15 +315,26 @@ def run_ours(args):
     # read complex int8 voltages + write the channelised data (2 B/complex int8, 4 B planar FP16)
     f_bytes = float(n_in * N * K * 2 + chan.numel() * chan.element_size())
     tensor = corr_uses_tc(args.xengine)
+    full_size = args.workload == "B"
     x_ach = x_flops / (x_ms * 1e-3) / 1e12
+    f_ach = f_bytes / (f_ms * 1e-3) / 1e9
     if tensor:
-        roof = {"bound": "tensor", "achieved": x_ach, "peak": peaks["bf16_sus"], "unit": "TFLOP/s",
-                "frac": x_ach / peaks["bf16_sus"], "traffic": None,
-                "kernel": "X-engine INT8-exact (tcgen05 kind::f16)",
-                "peak_note": f"{peaks['src']} sustained bf16 dense (fp16 runs at the same rate)"}
+        roof_x = {"bound": "tensor", "achieved": x_ach, "peak": peaks["bf16_sus"], "unit": "TFLOP/s",
+                  "frac": x_ach / peaks["bf16_sus"],
+                  "traffic": _traffic("k_xeng_tma") if (full_size and planar) else None,
+                  "kernel": "k_xeng_tma (X-engine INT8-exact, tcgen05 kind::f16)" if planar
+                  else "k_xeng_tc (X-engine INT8-exact, tcgen05 kind::f16)",
+                  "peak_note": f"{peaks['src']} sustained bf16 dense (fp16 runs at the same rate)",
+                  "algorithmic": f"{x_flops:.4g} FLOP per launch (8 per complex MAC over packed baselines)"}
     else:
-        roof = {"bound": "alu", "achieved": x_ach, "peak": None, "unit": "TOP/s", "frac": None,
-                "traffic": None, "kernel": "X-engine INT8 CUDA-core dp4a"}
+        roof_x = {"bound": "alu", "achieved": x_ach, "peak": None, "unit": "TOP/s", "frac": None,
+                  "traffic": None, "kernel": "k_xeng_i8 (CUDA-core dp4a)"}
+    roof_f = {"bound": "hbm", "achieved": f_ach, "peak": peaks["hbm"], "unit": "GB/s", "frac": f_ach / peaks["hbm"],
+              "traffic": _traffic("k_fengine") if (full_size and planar) else None,
+              "kernel": "k_fengine (FFT + int8 re-packing + corner turn)",
+              "peak_note": f"{peaks['src']} HBM copy bandwidth",
+              "algorithmic": f"{f_bytes:.4g} bytes per launch (read raw int8, write channelised data once)"}
+    roof = roof_f if f_ms >= x_ms else roof_x
     cpu = None
     if ws == 1 and not args.no_cpu:
         r, dt, cores, desc = cpu_oracle_sample(n_ant, n_pol, N, K, n_chan_sample=2, volt=volt_h)
@@ -332,6 +356,8 @@ def run_ours(args):
             "xengine_ms": cc_ms, "cmac_per_s": cmac_step / (cc_ms * 1e-3), "speedup_tensor_vs_cudacore": cc_ms / x_ms,
             "accuracy": "both exact (bit-identical INT32)"},
         "roofline": roof,
+        "roofline_xengine": roof_x,
+        "roofline_fengine": roof_f,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * cmac_step / (e2e_ms * 1e-3), "unit": "cMAC/s",
                 "h2d_bytes_per_step": int(volt.numel()), "d2h_bytes_per_step": int(vis_pin.numel() * 16),
