@@ -76,6 +76,13 @@ enum { CORR_XENG_AUTO = 0, CORR_XENG_CUDACORE = 1, CORR_XENG_TCGEN05 = 2 };
  *   (CORR_EUNSUPPORTED otherwise); doubles the channelised buffer's size. */
 enum { CORR_FLAG_PLANAR = 1 };
 
+/* CORR_FLAG_FUSED_DUMP (with CORR_FLAG_PLANAR): corr_xengine adds each
+ *   integration straight into the FP64 long-integration buffer from its epilogue
+ *   (the INT32 sums are exact, so the FP64 sums equal a separate dump's). There is
+ *   then no integration accumulator: corr_get_accum returns CORR_ESTATE, and
+ *   corr_dump only copies the FP64 buffer out. */
+enum { CORR_FLAG_FUSED_DUMP = 2 };
+
 typedef struct corr_opts {
     int32_t precision; /* CORR_PREC_*, default CORR_PREC_FP32 */
     int32_t xengine;   /* CORR_XENG_*, default CORR_XENG_AUTO */

@@ -22,6 +22,7 @@ CORR_EUNSUPPORTED = 7
 
 PREC = {"fp32": 0, "int8": 1, "fp16": 2, "fp16_hilo": 3}
 CORR_FLAG_PLANAR = 1
+CORR_FLAG_FUSED_DUMP = 2
 XENG = {"auto": 0, "cudacore": 1, "tcgen05": 2}
 
 

@@ -107,7 +107,8 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
     if (opts) o = *opts;
     if (o.precision < CORR_PREC_FP32 || o.precision > CORR_PREC_FP16_HILO) return CORR_EINVAL;
     if (o.xengine < CORR_XENG_AUTO || o.xengine > CORR_XENG_TCGEN05) return CORR_EINVAL;
-    if ((o.flags & ~CORR_FLAG_PLANAR) != 0) return CORR_EINVAL;
+    if ((o.flags & ~(CORR_FLAG_PLANAR | CORR_FLAG_FUSED_DUMP)) != 0) return CORR_EINVAL;
+    if ((o.flags & CORR_FLAG_FUSED_DUMP) && !(o.flags & CORR_FLAG_PLANAR)) return CORR_EUNSUPPORTED;
     if ((o.flags & CORR_FLAG_PLANAR) &&
         (o.precision != CORR_PREC_INT8 || o.xengine == CORR_XENG_CUDACORE || (n_spectra % 8) != 0))
         return CORR_EUNSUPPORTED;
@@ -224,7 +225,8 @@ corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, voi
     Handle &h = c->h;
     if (!corr::aligned16(chan_in)) return CORR_EINVAL;
     if (gains && h.precision == CORR_PREC_INT8) return CORR_EINVAL;
-    if (h.precision == CORR_PREC_INT8) {
+    if (h.precision == CORR_PREC_INT8 && !(h.flags & CORR_FLAG_FUSED_DUMP)) {
+        // the INT32 accumulator spans every call since the last dump
         if ((h.acc_spectra + h.n_spectra) * 2 * 127 * 127 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
     }
     corr::DeviceGuard dg(h.device);
@@ -247,6 +249,7 @@ corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, voi
 corr_status corr_get_accum(corr_t *c, void *out, void *stream) {
     if (!c || !out) return CORR_EINVAL;
     Handle &h = c->h;
+    if (h.flags & CORR_FLAG_FUSED_DUMP) return CORR_ESTATE;
     corr::DeviceGuard dg(h.device);
     CORR_CUDA_TRY(cudaMemcpyAsync(out, h.acc, (size_t)h.n_chan * h.n_base * 8, cudaMemcpyDeviceToDevice,
                                   corr::as_stream(stream)));
@@ -258,12 +261,12 @@ corr_status corr_dump(corr_t *c, double *vis_out, void *stream) {
     Handle &h = c->h;
     corr::DeviceGuard dg(h.device);
     cudaStream_t st = corr::as_stream(stream);
-    if (!h.acc_zero) {
+    if (!h.acc_zero && !(h.flags & CORR_FLAG_FUSED_DUMP)) {
         corr_status s = corr::launch_dump(h, st);
         if (s != CORR_OK) return s;
-        h.acc_zero = true;
-        h.acc_spectra = 0;
     }
+    h.acc_zero = true;
+    h.acc_spectra = 0;
     if (vis_out) {
         CORR_CUDA_TRY(cudaMemcpyAsync(vis_out, h.vis64, (size_t)h.n_chan * h.n_base * sizeof(double2),
                                       cudaMemcpyDeviceToDevice, st));

@@ -112,6 +112,17 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
+// Same for the 64-byte swizzle: rows of 64 B (32 fp16), 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;                                // swizzle: 64B
+    return d;
+}
+
 // Instruction descriptor for kind::f16: A, B fp16 K-major, D fp32, M x N.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool neg_a = false, bool neg_b = false) {
     return (1u << 4)                               // D format: F32

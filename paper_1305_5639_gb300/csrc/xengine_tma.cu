@@ -17,7 +17,7 @@
 // running sums held in registers. The result is bit-exact.
 //
 // Warp roles (384 threads, one persistent CTA per SM):
-//   warp 0       TMA producer (one thread): 3-stage ring of 64-spectrum stages
+//   warp 0       TMA producer (one thread): 6-stage ring of 32-spectrum stages
 //   warp 1       TMEM allocator + single-thread MMA issuer
 //   warps 4-11   epilogue, two warps per TMEM lane quarter, each owning half of
 //                the tile's columns and their INT32 sums
@@ -34,11 +34,11 @@ namespace corr {
 namespace {
 
 constexpr int TILE = 128;
-constexpr int KB = 64;                    // spectra per stage: 128 B of FP16 per row
-constexpr int PLANE = TILE * KB * 2;      // 16 KB per plane block
+constexpr int KB = 32;                    // spectra per stage: 64 B of FP16 per row (64B swizzle)
+constexpr int PLANE = TILE * KB * 2;      // 8 KB per plane block
 constexpr int STAGE_BYTES = 4 * PLANE;    // A_re, A_im, B_re, B_im
-constexpr int NSTAGE = 3;
-constexpr int CHUNK_KB = 8;               // INT8: fold every 512 spectra
+constexpr int NSTAGE = 6;                 // deep ring: TMA latency is hidden behind 5 stages of MMAs
+constexpr int CHUNK_KB = 16;              // INT8: fold every 512 spectra
 constexpr int NEPI = 256;                 // epilogue threads (warps 4..11)
 constexpr int NTHREADS = 384;
 constexpr int OFF_ARE = 0, OFF_AIM = PLANE, OFF_BRE = 2 * PLANE, OFF_BIM = 3 * PLANE;
@@ -48,6 +48,7 @@ enum Mode { kInt8 = 0, kFp16 = 1 };
 
 struct TParams {
     void *acc;
+    double2 *vis64;  // non-null: integrate straight into the FP64 long-integration buffer
     const float2 *gains;
     int *status;
     long long B;
@@ -179,8 +180,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                     for (int k = 0; k < KB / 16; ++k) {
                         const uint32_t ko = 32u * k;
                         const uint32_t acc = (kin > 0 || k > 0) ? 1u : 0u;
-                        const uint64_t dre = tc::desc_sw128(a_re + ko), dim = tc::desc_sw128(a_im + ko);
-                        const uint64_t bre = tc::desc_sw128(st + OFF_BRE + ko), bim = tc::desc_sw128(st + OFF_BIM + ko);
+                        const uint64_t dre = tc::desc_sw64(a_re + ko), dim = tc::desc_sw64(a_im + ko);
+                        const uint64_t bre = tc::desc_sw64(st + OFF_BRE + ko), bim = tc::desc_sw64(st + OFF_BIM + ko);
                         tc::mma_f16(d_re, dre, bre, ID, acc);
                         tc::mma_f16(d_re, dim, bim, ID, 1u);
                         tc::mma_f16(d_im, dim, bre, ID, acc);
@@ -238,7 +239,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                     tc::mbar_arrive(acce_bar(buf));
                 }
                 if (!alive) break;
-                if (i < p.n_in) {
+                if (i < p.n_in && p.vis64) {
+                    // fused dump: the exact INT32 tile sums go straight into the FP64 buffer
+                    double2 *row = p.vis64 + (size_t)chan * p.B + (size_t)i * (i + 1) / 2;
+#pragma unroll
+                    for (int x = 0; x < 64; ++x) {
+                        const int j = J0 + 64 * h + x;
+                        if (j <= i) {
+                            double2 o = row[j];
+                            o.x += (double)R[x];
+                            o.y += (double)R[64 + x];
+                            row[j] = o;
+                        }
+                    }
+                } else if (i < p.n_in) {
                     int2 *row = static_cast<int2 *>(p.acc) + (size_t)chan * p.B + (size_t)i * (i + 1) / 2;
 #pragma unroll
                     for (int x = 0; x < 64; ++x) {
@@ -280,12 +294,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                                     const float2 w = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
                                     v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
                                 }
-                                if (!p.store) {
-                                    const float2 o = row[j];
-                                    v.x += o.x;
-                                    v.y += o.y;
+                                if (p.vis64) {
+                                    double2 *r64 = p.vis64 + (size_t)chan * p.B + (size_t)i * (i + 1) / 2;
+                                    double2 o = r64[j];
+                                    o.x += (double)v.x;
+                                    o.y += (double)v.y;
+                                    r64[j] = o;
+                                } else {
+                                    if (!p.store) {
+                                        const float2 o = row[j];
+                                        v.x += o.x;
+                                        v.y += o.y;
+                                    }
+                                    row[j] = v;
                                 }
-                                row[j] = v;
                             }
                         }
                     }
@@ -342,7 +364,7 @@ corr_status launch_xengine_tma(const Handle &h, const void *planes, const float2
     const cuuint32_t box[4] = {KB, TILE, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(planes), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error_text("cuTensorMapEncodeTiled rejected the planar layout");
@@ -350,6 +372,7 @@ corr_status launch_xengine_tma(const Handle &h, const void *planes, const float2
     }
     TParams p;
     p.acc = h.acc;
+    p.vis64 = (h.flags & CORR_FLAG_FUSED_DUMP) ? h.vis64 : nullptr;
     p.gains = gains;
     p.status = h.status;
     p.B = h.n_base;

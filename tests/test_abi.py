@@ -60,12 +60,14 @@ def test_create_rejects_bad_arguments_without_device(lib):
     assert lib.corr_create(4, 1, 16, 16, None, None) == CORR_EINVAL
     o = corr_opts(9, 0, 0, -1)
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EINVAL
-    o = corr_opts(0, 0, 2, -1)  # unknown flag bit
+    o = corr_opts(0, 0, 4, -1)  # unknown flag bit
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EINVAL
     o = corr_opts(0, 0, 1, -1)  # the planar layout is INT8 only
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
     o = corr_opts(1, 0, 1, -1)  # ... and needs n_spectra % 8 == 0
     assert lib.corr_create(4, 1, 16, 12, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
+    o = corr_opts(1, 0, 2, -1)  # the fused dump needs the planar X-engine
+    assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
     # INT8 guard: n_spectra * 2 * 127^2 must stay below 2^31 (66573 spectra is the first to fail)
     o = corr_opts(1, 0, 0, -1)
     assert lib.corr_create(4, 1, 16, 66573, ctypes.byref(o), ctypes.byref(h)) == CORR_EOVERFLOW
