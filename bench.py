@@ -341,7 +341,8 @@ def run_ours(args):
     if ws == 1 and not args.no_cpu:
         r, dt, cores, desc = cpu_oracle_sample(n_ant, n_pol, N, K, n_chan_sample=2, volt=volt_h)
         cpu = {"value": r, "unit": "cMAC/s", "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
-    launches = 3  # F-engine, X-engine, dump per step (the calibration power pass is outside the timed region)
+    # per step: F-engine, X-engine (+ dump kernel unless fused); the calibration power pass is outside
+    launches = 2 if fused else 3
     line = {
         "metric": METRIC, "value": value, "unit": "cMAC/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
