@@ -17,7 +17,7 @@
 // running sums held in registers. The result is bit-exact.
 //
 // Warp roles (384 threads, one persistent CTA per SM):
-//   warp 0       TMA producer (one thread): 6-stage ring of 32-spectrum stages
+//   warp 0       TMA producer (one thread): 3-stage ring of 64-spectrum stages
 //   warp 1       TMEM allocator + single-thread MMA issuer
 //   warps 4-11   epilogue, two warps per TMEM lane quarter, each owning half of
 //                the tile's columns and their INT32 sums
@@ -34,15 +34,18 @@ namespace corr {
 namespace {
 
 constexpr int TILE = 128;
-constexpr int KB = 32;                    // spectra per stage: 64 B of FP16 per row (64B swizzle)
-constexpr int PLANE = TILE * KB * 2;      // 8 KB per plane block
+constexpr int KB = 64;                    // spectra per stage: 128 B of FP16 per row (128B swizzle)
+constexpr int PLANE = TILE * KB * 2;      // 16 KB per plane block
 constexpr int STAGE_BYTES = 4 * PLANE;    // A_re, A_im, B_re, B_im
-constexpr int NSTAGE = 6;                 // deep ring: TMA latency is hidden behind 5 stages of MMAs
-constexpr int CHUNK_KB = 16;              // INT8: fold every 512 spectra
+constexpr int NSTAGE = 3;
+constexpr int CHUNK_KB = 8;               // INT8: fold every 512 spectra
 constexpr int NEPI = 256;                 // epilogue threads (warps 4..11)
 constexpr int NTHREADS = 384;
 constexpr int OFF_ARE = 0, OFF_AIM = PLANE, OFF_BRE = 2 * PLANE, OFF_BIM = 3 * PLANE;
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
+constexpr int OSTG_WARP = 4096;           // per epilogue warp: a 32-row slice of the output tile
+constexpr int OFF_OSTG = NSTAGE * STAGE_BYTES;
+constexpr int OFF_BAR = OFF_OSTG + 8 * OSTG_WARP;
+constexpr int SMEM_BYTES = OFF_BAR + 1024 + 256;
 
 enum Mode { kInt8 = 0, kFp16 = 1 };
 
@@ -72,14 +75,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
     unsigned char *sgen = smem_raw + (sbase - raw);
-    const uint32_t bar0 = sbase + NSTAGE * STAGE_BYTES;
+    const uint32_t bar0 = sbase + OFF_BAR;
     // barriers: full[NSTAGE], empty[NSTAGE], accf[2], acce[2], drain; then tmem slot, abort flag
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (NSTAGE + s); };
     auto accf_bar = [&](int b) { return bar0 + 8u * (2 * NSTAGE + b); };
     auto acce_bar = [&](int b) { return bar0 + 8u * (2 * NSTAGE + 2 + b); };
     const uint32_t drain_bar = bar0 + 8u * (2 * NSTAGE + 4);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sgen + NSTAGE * STAGE_BYTES + 8 * (2 * NSTAGE + 5));
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sgen + OFF_BAR + 8 * (2 * NSTAGE + 5));
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -180,8 +183,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                     for (int k = 0; k < KB / 16; ++k) {
                         const uint32_t ko = 32u * k;
                         const uint32_t acc = (kin > 0 || k > 0) ? 1u : 0u;
-                        const uint64_t dre = tc::desc_sw64(a_re + ko), dim = tc::desc_sw64(a_im + ko);
-                        const uint64_t bre = tc::desc_sw64(st + OFF_BRE + ko), bim = tc::desc_sw64(st + OFF_BIM + ko);
+                        const uint64_t dre = tc::desc_sw128(a_re + ko), dim = tc::desc_sw128(a_im + ko);
+                        const uint64_t bre = tc::desc_sw128(st + OFF_BRE + ko), bim = tc::desc_sw128(st + OFF_BIM + ko);
                         tc::mma_f16(d_re, dre, bre, ID, acc);
                         tc::mma_f16(d_re, dim, bim, ID, 1u);
                         tc::mma_f16(d_im, dim, bre, ID, acc);
@@ -239,33 +242,60 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                     tc::mbar_arrive(acce_bar(buf));
                 }
                 if (!alive) break;
-                if (i < p.n_in && p.vis64) {
-                    // fused dump: the exact INT32 tile sums go straight into the FP64 buffer
-                    double2 *row = p.vis64 + (size_t)chan * p.B + (size_t)i * (i + 1) / 2;
+                // write the tile's INT32 sums through a per-warp shared-memory slice so that
+                // every global row segment is written (or read-modify-written) contiguously
+                unsigned char *ostg = sgen + OFF_OSTG + ew * OSTG_WARP;
+                const long long rbase = (long long)chan * p.B;
+                if (p.vis64) {
+                    // 8 double2 per row slice: 32 rows x 128 B
+                    double2 *sl = reinterpret_cast<double2 *>(ostg);
 #pragma unroll
-                    for (int x = 0; x < 64; ++x) {
-                        const int j = J0 + 64 * h + x;
-                        if (j <= i) {
-                            double2 o = row[j];
-                            o.x += (double)R[x];
-                            o.y += (double)R[64 + x];
-                            row[j] = o;
-                        }
-                    }
-                } else if (i < p.n_in) {
-                    int2 *row = static_cast<int2 *>(p.acc) + (size_t)chan * p.B + (size_t)i * (i + 1) / 2;
+                    for (int sc = 0; sc < 8; ++sc) {
 #pragma unroll
-                    for (int x = 0; x < 64; ++x) {
-                        const int j = J0 + 64 * h + x;
-                        if (j <= i) {
-                            int2 o = make_int2(R[x], R[64 + x]);
-                            if (!p.store) {
-                                const int2 q = row[j];
-                                o.x += q.x;
-                                o.y += q.y;
+                        for (int x = 0; x < 8; ++x)
+                            sl[lane * 8 + ((x + lane) & 7)] = make_double2((double)R[8 * sc + x], (double)R[64 + 8 * sc + x]);
+                        __syncwarp();
+#pragma unroll
+                        for (int rr = 0; rr < 8; ++rr) {
+                            const int r = rr * 4 + (lane >> 3), e = lane & 7;
+                            const int ii = I0 + wq * 32 + r, jj = J0 + 64 * h + 8 * sc + e;
+                            if (ii < p.n_in && jj <= ii) {
+                                double2 *dst = p.vis64 + rbase + (long long)ii * (ii + 1) / 2 + jj;
+                                const double2 v = sl[r * 8 + ((e + r) & 7)];
+                                double2 o = *dst;
+                                o.x += v.x;
+                                o.y += v.y;
+                                *dst = o;
                             }
-                            row[j] = o;
                         }
+                        __syncwarp();
+                    }
+                } else {
+                    // 16 int2 per row slice: 32 rows x 128 B
+                    int2 *sl = reinterpret_cast<int2 *>(ostg);
+                    int2 *acc = static_cast<int2 *>(p.acc);
+#pragma unroll
+                    for (int sc = 0; sc < 4; ++sc) {
+#pragma unroll
+                        for (int x = 0; x < 16; ++x)
+                            sl[lane * 16 + ((x + lane) & 15)] = make_int2(R[16 * sc + x], R[64 + 16 * sc + x]);
+                        __syncwarp();
+#pragma unroll
+                        for (int rr = 0; rr < 16; ++rr) {
+                            const int r = rr * 2 + (lane >> 4), e = lane & 15;
+                            const int ii = I0 + wq * 32 + r, jj = J0 + 64 * h + 16 * sc + e;
+                            if (ii < p.n_in && jj <= ii) {
+                                int2 *dst = acc + rbase + (long long)ii * (ii + 1) / 2 + jj;
+                                int2 v = sl[r * 16 + ((e + r) & 15)];
+                                if (!p.store) {
+                                    const int2 o = *dst;
+                                    v.x += o.x;
+                                    v.y += o.y;
+                                }
+                                *dst = v;
+                            }
+                        }
+                        __syncwarp();
                     }
                 }
             } else {
@@ -364,7 +394,7 @@ corr_status launch_xengine_tma(const Handle &h, const void *planes, const float2
     const cuuint32_t box[4] = {KB, TILE, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(planes), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error_text("cuTensorMapEncodeTiled rejected the planar layout");
