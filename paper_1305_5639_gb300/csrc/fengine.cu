@@ -58,10 +58,11 @@ constexpr float kMagic = 12582912.0f;
 
 __device__ __forceinline__ uint32_t pack_q(float2 v, float sc) {
     // Re-pack to int8: clamp(S * scale) to [-127, 127], round half to even.
-    const float re = fminf(fmaxf(v.x * sc, -127.0f), 127.0f) + kMagic;
-    const float im = fminf(fmaxf(v.y * sc, -127.0f), 127.0f) + kMagic;
+    float2 t = f2_mul(v, make_float2(sc, sc));
+    t = make_float2(fminf(fmaxf(t.x, -127.0f), 127.0f), fminf(fmaxf(t.y, -127.0f), 127.0f));
+    t = f2_add(t, make_float2(kMagic, kMagic));
     // low byte of each result is the two's-complement int8 code
-    return __byte_perm(__float_as_uint(re), __float_as_uint(im), 0x0040);
+    return __byte_perm(__float_as_uint(t.x), __float_as_uint(t.y), 0x0040);
 }
 
 // Two complex int8 codes [re0 im0 re1 im1] -> FP16 pairs (re0, re1) and (im0, im1),
@@ -80,8 +81,9 @@ __device__ __forceinline__ void codes_to_f16_planes(uint32_t w, uint32_t &re, ui
 // (0x4B400000 | (x + 128)) is the float 12582912 + x + 128.
 __device__ __forceinline__ float2 i8_to_f2(uint32_t w) {
     const uint32_t u = w ^ 0x8080u;
-    return make_float2(__uint_as_float(__byte_perm(u, 0x4B400000u, 0x7650)) - (kMagic + 128.0f),
-                       __uint_as_float(__byte_perm(u, 0x4B400000u, 0x7651)) - (kMagic + 128.0f));
+    return f2_sub(make_float2(__uint_as_float(__byte_perm(u, 0x4B400000u, 0x7650)),
+                              __uint_as_float(__byte_perm(u, 0x4B400000u, 0x7651))),
+                  make_float2(kMagic + 128.0f, kMagic + 128.0f));
 }
 
 template <int N, bool I8, int MODE>

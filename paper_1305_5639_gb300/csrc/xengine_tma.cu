@@ -255,18 +255,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                         for (int x = 0; x < 8; ++x)
                             sl[lane * 8 + ((x + lane) & 7)] = make_double2((double)R[8 * sc + x], (double)R[64 + 8 * sc + x]);
                         __syncwarp();
+                        // all eight row reads in flight before any write (latency, not bandwidth,
+                        // bounds this read-modify-write)
+                        double2 o[8];
 #pragma unroll
                         for (int rr = 0; rr < 8; ++rr) {
                             const int r = rr * 4 + (lane >> 3), e = lane & 7;
                             const int ii = I0 + wq * 32 + r, jj = J0 + 64 * h + 8 * sc + e;
-                            if (ii < p.n_in && jj <= ii) {
-                                double2 *dst = p.vis64 + rbase + (long long)ii * (ii + 1) / 2 + jj;
-                                const double2 v = sl[r * 8 + ((e + r) & 7)];
-                                double2 o = *dst;
-                                o.x += v.x;
-                                o.y += v.y;
-                                *dst = o;
-                            }
+                            o[rr] = (ii < p.n_in && jj <= ii)
+                                        ? __ldcg(p.vis64 + rbase + (long long)ii * (ii + 1) / 2 + jj)
+                                        : make_double2(0.0, 0.0);
+                        }
+#pragma unroll
+                        for (int rr = 0; rr < 8; ++rr) {
+                            const int r = rr * 4 + (lane >> 3), e = lane & 7;
+                            const int ii = I0 + wq * 32 + r, jj = J0 + 64 * h + 8 * sc + e;
+                            const double2 v = sl[r * 8 + ((e + r) & 7)];
+                            if (ii < p.n_in && jj <= ii)
+                                p.vis64[rbase + (long long)ii * (ii + 1) / 2 + jj] =
+                                    make_double2(o[rr].x + v.x, o[rr].y + v.y);
                         }
                         __syncwarp();
                     }
