@@ -53,6 +53,8 @@ void free_buffers(Handle &h) {
     cudaFree(h.status);
     cudaFree(h.power64);
     cudaFree(h.bwd_ws);
+    cudaFree(h.planar_ws);
+    h.planar_ws = nullptr;
     h.acc = nullptr;
     h.vis64 = nullptr;
     h.twiddle = nullptr;
@@ -233,12 +235,33 @@ corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, voi
     const bool store = h.acc_zero;
     const float2 *g = reinterpret_cast<const float2 *>(gains);
     corr_status s;
-    if (h.flags & CORR_FLAG_PLANAR)
-        s = corr::launch_xengine_tma(h, chan_in, g, store, corr::as_stream(stream));
-    else if (corr::use_tc(h))
-        s = corr::launch_xengine_tc(h, chan_in, g, store, corr::as_stream(stream));
+    cudaStream_t st = corr::as_stream(stream);
+    const bool fp16 = h.precision == CORR_PREC_FP16 || h.precision == CORR_PREC_FP16_HILO;
+    if (h.flags & CORR_FLAG_PLANAR) {
+        s = corr::launch_xengine_tma(h, chan_in, 2, g, store, st);
+    } else if (fp16 && (h.precision == CORR_PREC_FP16_HILO || h.xengine == CORR_XENG_AUTO) &&
+               corr::xengine_tma_supported(h)) {
+        // FP16 tensor-core path: one pass to planar FP16 operands, then the TMA X-engine
+        const int npl = h.precision == CORR_PREC_FP16_HILO ? 4 : 2;
+        const size_t need = (size_t)h.n_chan * npl * h.n_in * h.n_spectra * 2;
+        if (h.planar_ws_bytes < need) {
+            cudaFree(h.planar_ws);
+            h.planar_ws = nullptr;
+            h.planar_ws_bytes = 0;
+            if (cudaMalloc(&h.planar_ws, need) != cudaSuccess) {
+                cudaGetLastError();
+                return CORR_ENOMEM;
+            }
+            h.planar_ws_bytes = need;
+        }
+        s = corr::launch_to_planar(h, static_cast<const float2 *>(chan_in), h.planar_ws, npl, st);
+        if (s == CORR_OK) s = corr::launch_xengine_tma(h, h.planar_ws, npl, g, store, st);
+    } else if (h.precision == CORR_PREC_FP16_HILO) {
+        s = CORR_EUNSUPPORTED;  // the hi/lo products need the TMA path (n_spectra % 8 == 0)
+    } else if (corr::use_tc(h))
+        s = corr::launch_xengine_tc(h, chan_in, g, store, st);
     else
-        s = corr::launch_xengine_cudacore(h, chan_in, g, store, corr::as_stream(stream));
+        s = corr::launch_xengine_cudacore(h, chan_in, g, store, st);
     if (s == CORR_OK) {
         h.acc_zero = false;
         h.acc_spectra += h.n_spectra;

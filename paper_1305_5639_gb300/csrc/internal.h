@@ -23,6 +23,8 @@ struct Handle {
     float2 *twiddle = nullptr;   // F-engine twiddles W_N^(t k1), [k1][t], N = T x T
     int32_t *status = nullptr;   // device status word (0 ok, else CORR_* code set by a kernel)
     double *power64 = nullptr;   // [n_chan] scratch for corr_fengine_power
+    void *planar_ws = nullptr;   // FP16 operand planes for the FP16 tensor-core paths (first use)
+    size_t planar_ws_bytes = 0;
     float2 *bwd_ws = nullptr;    // dg partials for corr_backward (allocated on first use)
     size_t bwd_ws_bytes = 0;
 };
@@ -56,8 +58,9 @@ corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const fl
                                cudaStream_t st);
 bool fengine_supported(int n_chan);
 bool xengine_tma_supported(const Handle &h);
-corr_status launch_xengine_tma(const Handle &h, const void *planes, const float2 *gains, bool store,
+corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
                                cudaStream_t st);
+corr_status launch_to_planar(const Handle &h, const float2 *X, void *out, int npl, cudaStream_t st);
 
 // Bounded-wait iteration limit for device-side spins (mbarrier waits).
 constexpr long long kSpinLimit = 1LL << 26;

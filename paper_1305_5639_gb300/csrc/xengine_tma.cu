@@ -34,18 +34,31 @@ namespace corr {
 namespace {
 
 constexpr int TILE = 128;
-constexpr int KB = 64;                    // spectra per stage: 128 B of FP16 per row (128B swizzle)
-constexpr int PLANE = TILE * KB * 2;      // 16 KB per plane block
-constexpr int STAGE_BYTES = 4 * PLANE;    // A_re, A_im, B_re, B_im
 constexpr int NSTAGE = 3;
-constexpr int CHUNK_KB = 8;               // INT8: fold every 512 spectra
 constexpr int NEPI = 256;                 // epilogue threads (warps 4..11)
 constexpr int NTHREADS = 384;
-constexpr int OFF_ARE = 0, OFF_AIM = PLANE, OFF_BRE = 2 * PLANE, OFF_BIM = 3 * PLANE;
 constexpr int OSTG_WARP = 4096;           // per epilogue warp: a 32-row slice of the output tile
-constexpr int OFF_OSTG = NSTAGE * STAGE_BYTES;
-constexpr int OFF_BAR = OFF_OSTG + 8 * OSTG_WARP;
-constexpr int SMEM_BYTES = OFF_BAR + 1024 + 256;
+
+// Stage geometry. NPL planes per operand side (2: Re, Im; 4: Re_h, Im_h, Re_l, Im_l
+// of the hi/lo split); KB spectra per stage: 64 (128-byte rows, 128B swizzle) or
+// 32 (64-byte rows, 64B swizzle). A stage holds the NPL planes of the I block
+// followed by the NPL planes of the J block.
+template <int NPL_, int KB_>
+struct TCfg {
+    static constexpr int NPL = NPL_;
+    static constexpr int KB = KB_;
+    static constexpr int PLANE = TILE * KB * 2;
+    static constexpr int STAGE_BYTES = 2 * NPL * PLANE;
+    static constexpr int CHUNK_KB = 512 / KB;  // INT8: fold every 512 spectra
+    static constexpr int OFF_OSTG = NSTAGE * STAGE_BYTES;
+    static constexpr int OFF_BAR = OFF_OSTG + 8 * OSTG_WARP;
+    static constexpr int SMEM_BYTES = OFF_BAR + 1024 + 256;
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+    static __device__ __forceinline__ uint64_t desc(uint32_t a) {
+        if constexpr (KB == 64) return tc::desc_sw128(a);
+        else return tc::desc_sw64(a);
+    }
+};
 
 enum Mode { kInt8 = 0, kFp16 = 1 };
 
@@ -69,8 +82,10 @@ __device__ __forceinline__ void decode(long long item, int n_tiles, int &chan, i
     bj = t - r * (r + 1) / 2;
 }
 
-template <int MODE>
+template <int MODE, class C>
 __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant__ CUtensorMap tmap, const TParams p) {
+    constexpr int KB = C::KB, NPL = C::NPL, PLANE = C::PLANE, STAGE_BYTES = C::STAGE_BYTES;
+    constexpr int CHUNK_KB = C::CHUNK_KB, OFF_OSTG = C::OFF_OSTG, OFF_BAR = C::OFF_BAR;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -130,13 +145,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                         break;
                     }
                     const uint32_t st = sbase + slot * STAGE_BYTES;
-                    tc::mbar_arrive_expect_tx(full_bar(slot), diag ? 2 * PLANE : 4 * PLANE);
+                    tc::mbar_arrive_expect_tx(full_bar(slot), (diag ? NPL : 2 * NPL) * PLANE);
                     const int s0 = kb * KB;
-                    tc::tma_load_4d(st + OFF_BRE, &tmap, s0, bj * TILE, 0, chan, full_bar(slot));
-                    tc::tma_load_4d(st + OFF_BIM, &tmap, s0, bj * TILE, 1, chan, full_bar(slot));
-                    if (!diag) {
-                        tc::tma_load_4d(st + OFF_ARE, &tmap, s0, bi * TILE, 0, chan, full_bar(slot));
-                        tc::tma_load_4d(st + OFF_AIM, &tmap, s0, bi * TILE, 1, chan, full_bar(slot));
+#pragma unroll
+                    for (int pl = 0; pl < NPL; ++pl) {
+                        tc::tma_load_4d(st + (NPL + pl) * PLANE, &tmap, s0, bj * TILE, pl, chan, full_bar(slot));
+                        if (!diag) tc::tma_load_4d(st + pl * PLANE, &tmap, s0, bi * TILE, pl, chan, full_bar(slot));
                     }
                 }
                 if (!ok) break;
@@ -177,18 +191,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                     }
                     tc::tc_fence_after();
                     const uint32_t st = sbase + slot * STAGE_BYTES;
-                    const uint32_t a_re = st + (diag ? OFF_BRE : OFF_ARE);
-                    const uint32_t a_im = st + (diag ? OFF_BIM : OFF_AIM);
+                    const uint32_t a0 = st + (diag ? NPL * PLANE : 0), b0 = st + NPL * PLANE;
+                    // complex product of (Re, Im) planes (a, a + PLANE) and (b, b + PLANE):
+                    // Re += ar br + ai bi, Im += ai br - ar bi
+                    auto cmma = [&](uint32_t a, uint32_t b, uint32_t ko, uint32_t acc) {
+                        const uint64_t ar = C::desc(a + ko), ai = C::desc(a + PLANE + ko);
+                        const uint64_t br = C::desc(b + ko), bi = C::desc(b + PLANE + ko);
+                        tc::mma_f16(d_re, ar, br, ID, acc);
+                        tc::mma_f16(d_re, ai, bi, ID, 1u);
+                        tc::mma_f16(d_im, ai, br, ID, acc);
+                        tc::mma_f16(d_im, ar, bi, ID_NEG, 1u);
+                    };
 #pragma unroll
                     for (int k = 0; k < KB / 16; ++k) {
                         const uint32_t ko = 32u * k;
-                        const uint32_t acc = (kin > 0 || k > 0) ? 1u : 0u;
-                        const uint64_t dre = tc::desc_sw128(a_re + ko), dim = tc::desc_sw128(a_im + ko);
-                        const uint64_t bre = tc::desc_sw128(st + OFF_BRE + ko), bim = tc::desc_sw128(st + OFF_BIM + ko);
-                        tc::mma_f16(d_re, dre, bre, ID, acc);
-                        tc::mma_f16(d_re, dim, bim, ID, 1u);
-                        tc::mma_f16(d_im, dim, bre, ID, acc);
-                        tc::mma_f16(d_im, dre, bim, ID_NEG, 1u);
+                        cmma(a0, b0, ko, (kin > 0 || k > 0) ? 1u : 0u);  // h h
+                        if constexpr (NPL == 4) {
+                            cmma(a0, b0 + 2 * PLANE, ko, 1u);           // h l
+                            cmma(a0 + 2 * PLANE, b0, ko, 1u);           // l h
+                        }
                     }
                     tc::mma_commit(empty_bar(slot));
                     if (kin == chunk_kb - 1 || kb == nkb - 1) {
@@ -385,24 +406,25 @@ EncodeTiledFn encode_fn() {
 
 bool xengine_tma_supported(const Handle &h) { return (h.n_spectra % 8) == 0 && encode_fn() != nullptr; }
 
-corr_status launch_xengine_tma(const Handle &h, const void *planes, const float2 *gains, bool store,
+corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
                                cudaStream_t st) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
         set_error_text("cuTensorMapEncodeTiled is not available from the driver");
         return CORR_EUNSUPPORTED;
     }
-    if ((h.n_spectra % 8) != 0) return CORR_EUNSUPPORTED;
+    if ((h.n_spectra % 8) != 0 || (npl != 2 && npl != 4)) return CORR_EUNSUPPORTED;
+    const int kb = npl == 2 ? 64 : 32;
     // planar FP16 tensor: dims (innermost first) spectrum, input, plane, channel
     CUtensorMap tmap;
-    const cuuint64_t dims[4] = {(cuuint64_t)h.n_spectra, (cuuint64_t)h.n_in, 2, (cuuint64_t)h.n_chan};
+    const cuuint64_t dims[4] = {(cuuint64_t)h.n_spectra, (cuuint64_t)h.n_in, (cuuint64_t)npl, (cuuint64_t)h.n_chan};
     const cuuint64_t strides[3] = {(cuuint64_t)h.n_spectra * 2, (cuuint64_t)h.n_spectra * 2 * h.n_in,
-                                   (cuuint64_t)h.n_spectra * 2 * h.n_in * 2};
-    const cuuint32_t box[4] = {KB, TILE, 1, 1};
+                                   (cuuint64_t)h.n_spectra * 2 * h.n_in * npl};
+    const cuuint32_t box[4] = {(cuuint32_t)kb, TILE, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(planes), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, kb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error_text("cuTensorMapEncodeTiled rejected the planar layout");
         return CORR_EINVAL;
@@ -419,13 +441,19 @@ corr_status launch_xengine_tma(const Handle &h, const void *planes, const float2
     p.n_in = h.n_in;
     p.K = h.n_spectra;
     p.store = store ? 1 : 0;
-    const long long grid = p.n_items < h.n_sm ? p.n_items : h.n_sm;
+    const unsigned grid = (unsigned)(p.n_items < h.n_sm ? p.n_items : h.n_sm);
     if (h.precision == CORR_PREC_INT8) {
-        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-        k_xeng_tma<kInt8><<<(unsigned)grid, NTHREADS, SMEM_BYTES, st>>>(tmap, p);
+        using C = TCfg<2, 64>;
+        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+        k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, p);
+    } else if (npl == 2) {
+        using C = TCfg<2, 64>;
+        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, p);
     } else {
-        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-        k_xeng_tma<kFp16><<<(unsigned)grid, NTHREADS, SMEM_BYTES, st>>>(tmap, p);
+        using C = TCfg<4, 32>;
+        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, p);
     }
     return check_launch("k_xeng_tma");
 }

@@ -211,3 +211,50 @@ def test_tma_fused_dump_equals_separate_dump(cuda_ok):
         c.xengine(torch.from_numpy(to_planar(parts[0])).to(DEV))
     c.check_status()
     c.close()
+
+
+# --------------------------------------------------------------------------- FP16 hi/lo and plain on the TMA path
+@pytest.mark.parametrize("prec,tol", [("fp16", 2e-3), ("fp16_hilo", 5e-5)])
+@pytest.mark.parametrize("n_in,K,n_chan", [(128, 256, 2), (250, 200, 2), (300, 520, 1)])
+def test_tma_fp16_paths(cuda_ok, prec, tol, n_in, K, n_chan):
+    X = synth.chan_sources(n_chan, n_in, K, n_src=3, seed=n_in, src_amp=0.1)
+    c = api.Correlator(n_in, 1, n_chan, K, precision=prec)
+    c.xengine(torch.from_numpy(X).to(DEV))
+    V = c.accum().cpu().numpy().astype(np.complex128)
+    c.check_status()
+    emax, erms = norm_err(V, oracle.cmac(X), n_in)
+    assert emax <= tol, (emax, erms)
+    c.close()
+
+
+def test_tma_fp16_hilo_gains_and_converter_fp16(cuda_ok):
+    n_in, K, n_chan = 140, 128, 2
+    X = synth.chan_sources(n_chan, n_in, K, n_src=3, seed=8, src_amp=0.1)
+    g = synth.gains(n_in, seed=8)
+    ref = oracle.apply_gains(oracle.cmac(X), g, n_in)
+    for prec, eng, tol in (("fp16_hilo", "auto", 5e-5), ("fp16", "tcgen05", 2e-3)):
+        c = api.Correlator(n_in, 1, n_chan, K, precision=prec, xengine=eng)
+        c.xengine(torch.from_numpy(X).to(DEV), torch.from_numpy(g).to(DEV))
+        V = c.accum().cpu().numpy().astype(np.complex128)
+        emax, _ = norm_err(V, ref, n_in)
+        assert emax <= tol, (prec, eng, emax)
+        c.close()
+
+
+def test_fp16_workload_channel_two_integrations(cuda_ok):
+    """The FP16 workload's full channel shape (1024 antennas x 2 pol = 2048 inputs,
+    2048 spectra per integration, 3 sources) on one channel, two integrations dumped
+    to FP64, plain FP16 and hi/lo, against the oracle."""
+    n_in, K = 2048, 2048
+    chans = [1234]
+    parts = [synth.chan_sources(4096, n_in, K, n_src=3, seed=21 + t, chans=chans, src_amp=0.1) for t in range(2)]
+    ref = oracle.dump([oracle.cmac(X) for X in parts])
+    for prec, tol in (("fp16", 2e-3), ("fp16_hilo", 5e-5)):
+        c = api.Correlator(1024, 2, 1, K, precision=prec)
+        for X in parts:
+            c.xengine(torch.from_numpy(X).to(DEV))
+            c.dump(copy=False)
+        vis = c.dump().cpu().numpy()
+        emax, erms = norm_err(vis, ref, n_in)
+        assert emax <= tol, (prec, emax, erms)
+        c.close()
