@@ -199,6 +199,50 @@ CORR_API corr_status corr_reset(corr_t *h, void *stream);
 CORR_API corr_status corr_backward(corr_t *h, const float *grad_vis, const void *chan_in, const float *gains,
                           float *grad_chan, float *grad_gains, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched X-engine: many independent sub-arrays correlated (Eq. 2, INT8 exact)
+ * by one persistent tensor-core launch that is captured once in a CUDA graph and
+ * replayed. Inputs are planar FP16 int8 codes (the CORR_FLAG_PLANAR layout, e.g.
+ * written by corr_fengine); outputs are INT32 pairs, overwritten by each run.
+ * Pointers are fixed at create time: to process another window of data, write it
+ * into the same buffers and run again.
+ * ------------------------------------------------------------------------- */
+typedef struct corr_batch_s corr_batch_t;
+
+typedef struct corr_sub_desc {
+    int32_t n_in;       /* inputs of the sub-array (1..65535) */
+    int32_t n_chan;     /* channels */
+    int32_t n_spectra;  /* spectra per integration: a multiple of 8, with n_spectra * 2 * 127^2 < 2^31 */
+    int32_t reserved;   /* must be 0 */
+    const void *planes; /* device, [n_chan][2][n_in][n_spectra] FP16 codes, 16-byte aligned */
+    int32_t *vis;       /* device, [n_chan][n_in (n_in + 1) / 2][2] INT32, 8-byte aligned */
+} corr_sub_desc;
+
+/* Plan a batch on the current device: every (sub-array, channel, lower-triangle
+ * tile) work item is spread over one CTA per SM, longest first. The descriptor
+ * array is copied; the device buffers it names must outlive the batch. */
+CORR_API corr_status corr_batch_create(int32_t n_sub, const corr_sub_desc *subs, corr_batch_t **out);
+
+/* Choose each sub-array's tile shape by timing: sub-arrays of <= 64 (<= 32)
+ * inputs may pack 2 (up to 4) channels into one 128-row tensor-core tile. The
+ * choices are read from / written to the JSON file cache_path (NULL: no cache)
+ * keyed by (inputs, spectra), and the batch is re-planned. Synchronises stream;
+ * runs the sub-arrays (overwriting their outputs) while timing. */
+CORR_API corr_status corr_batch_tune(corr_batch_t *b, const char *cache_path, void *stream);
+
+/* Correlate every sub-array: one graph launch on `stream` (the graph is captured
+ * on the first run after create or tune). */
+CORR_API corr_status corr_batch_run(corr_batch_t *b, void *stream);
+
+/* Read and clear the batch's device status word (CORR_ETIMEOUT if the kernel
+ * gave up on a bounded wait). Synchronises stream. */
+CORR_API corr_status corr_batch_check_status(corr_batch_t *b, void *stream);
+
+/* Channels per tile chosen for sub-array `sub` (1, 2 or 4), -1 on bad arguments. */
+CORR_API int32_t corr_batch_channels_per_tile(const corr_batch_t *b, int32_t sub);
+
+CORR_API corr_status corr_batch_destroy(corr_batch_t *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,11 @@ class corr_opts(ctypes.Structure):
                 ("device", ctypes.c_int32)]
 
 
+class corr_sub_desc(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("n_chan", ctypes.c_int32), ("n_spectra", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("planes", ctypes.c_void_p), ("vis", ctypes.c_void_p)]
+
+
 # (name, restype, argtypes) for every symbol of include/corr.h
 _P = ctypes.c_void_p
 _S = ctypes.c_int32
@@ -51,6 +56,12 @@ SIGNATURES = [
     ("corr_backward", _S, [_P, _P, _P, _P, _P, _P, _P]),
     ("corr_fengine_power_noalloc", _S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         _P, _P]),
+    ("corr_batch_create", _S, [ctypes.c_int32, ctypes.POINTER(corr_sub_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    ("corr_batch_tune", _S, [_P, ctypes.c_char_p, _P]),
+    ("corr_batch_run", _S, [_P, _P]),
+    ("corr_batch_check_status", _S, [_P, _P]),
+    ("corr_batch_channels_per_tile", ctypes.c_int32, [_P, ctypes.c_int32]),
+    ("corr_batch_destroy", _S, [_P]),
 ]
 
 _lib = None

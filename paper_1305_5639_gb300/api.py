@@ -175,3 +175,74 @@ class Correlator:
         gg = torch.empty(self.n_in, dtype=torch.complex64, device=self.device) if want_gains else None
         corr_backward(self.h, grad_vis, chan_in, gains, gc, gg, stream)
         return gc, gg
+
+
+def corr_batch_create(subs) -> ctypes.c_void_p:
+    """subs: sequence of (planes, n_in, n_chan, n_spectra, vis) with device tensors."""
+    arr = (_lib.corr_sub_desc * len(subs))()
+    for k, (planes, n_in, n_chan, K, vis) in enumerate(subs):
+        arr[k] = _lib.corr_sub_desc(int(n_in), int(n_chan), int(K), 0, _ptr(planes), _ptr(vis))
+    b = ctypes.c_void_p()
+    check(_lib.load().corr_batch_create(len(subs), arr, ctypes.byref(b)), "corr_batch_create")
+    return b
+
+
+def corr_batch_tune(b, cache_path=None, stream=None) -> None:
+    check(_lib.load().corr_batch_tune(b, None if cache_path is None else str(cache_path).encode(), _stream(stream)),
+          "corr_batch_tune")
+
+
+def corr_batch_run(b, stream=None) -> None:
+    check(_lib.load().corr_batch_run(b, _stream(stream)), "corr_batch_run")
+
+
+def corr_batch_check_status(b, stream=None) -> None:
+    check(_lib.load().corr_batch_check_status(b, _stream(stream)), "corr_batch_check_status")
+
+
+def corr_batch_channels_per_tile(b, sub: int) -> int:
+    return int(_lib.load().corr_batch_channels_per_tile(b, int(sub)))
+
+
+def corr_batch_destroy(b) -> None:
+    check(_lib.load().corr_batch_destroy(b), "corr_batch_destroy")
+
+
+class Batch:
+    """Batched INT8 X-engine over sub-arrays given as planar FP16 code tensors
+    [n_chan, 2, n_in, n_spectra]; allocates one INT32 output per sub-array."""
+
+    def __init__(self, planes_list):
+        self.planes = [p.contiguous() for p in planes_list]
+        self.vis = []
+        subs = []
+        for p in self.planes:
+            n_chan, two, n_in, K = p.shape
+            assert two == 2 and p.dtype == torch.float16
+            v = torch.zeros((n_chan, n_in * (n_in + 1) // 2, 2), dtype=torch.int32, device=p.device)
+            self.vis.append(v)
+            subs.append((p, n_in, n_chan, K, v))
+        self.b = corr_batch_create(subs)
+
+    def tune(self, cache_path=None, stream=None):
+        corr_batch_tune(self.b, cache_path, stream)
+
+    def run(self, stream=None):
+        corr_batch_run(self.b, stream)
+
+    def check_status(self, stream=None):
+        corr_batch_check_status(self.b, stream)
+
+    def channels_per_tile(self, sub):
+        return corr_batch_channels_per_tile(self.b, sub)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            corr_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

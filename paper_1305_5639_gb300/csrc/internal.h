@@ -62,6 +62,22 @@ corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, con
                                cudaStream_t st);
 corr_status launch_to_planar(const Handle &h, const float2 *X, void *out, int npl, cudaStream_t st);
 
+// One sub-array of a batched X-engine launch (device-side descriptor).
+struct BatchSub {
+    void *acc;    // INT32 pairs [n_chan][B] (overwritten)
+    long long B;  // packed pairs n_in (n_in + 1) / 2
+    int n_in, K, n_chan;
+    int cpt;      // channels packed per 128-row tile (1, 2 or 4; n_in <= 128 / cpt)
+};
+
+// Tensor map of a planar FP16 operand [n_chan][npl][n_in][K] with boxes of
+// (64 spectra x box_rows inputs), 128B swizzle (CUtensorMap storage, 128 bytes).
+corr_status tma_encode_planar(void *tmap128, const void *planes, int n_in, int n_chan, int K, int npl,
+                              int box_rows);
+// One persistent launch over a precomputed work list (see batch.cu).
+corr_status launch_xengine_tma_batch(const void *d_tmaps, const BatchSub *d_subs, const int4 *d_items,
+                                     const int *d_cta_off, int grid, int *status, cudaStream_t st);
+
 // Bounded-wait iteration limit for device-side spins (mbarrier waits).
 constexpr long long kSpinLimit = 1LL << 26;
 

@@ -62,15 +62,65 @@ struct TCfg {
 
 enum Mode { kInt8 = 0, kFp16 = 1 };
 
+using SubDesc = BatchSub;
+
 struct TParams {
     void *acc;
     double2 *vis64;  // non-null: integrate straight into the FP64 long-integration buffer
+    // batched launch (batch != 0): per-sub tensor maps and descriptors, and each CTA's
+    // slice [cta_off[b], cta_off[b + 1]) of the item list (sub, chan, bi | bj << 16)
+    const CUtensorMap *tmaps;
+    const SubDesc *subs;
+    const int4 *items;
+    const int *cta_off;
+    int batch;
     const float2 *gains;
     int *status;
     long long B;
     long long n_items;
     int n_in, K, n_tiles, store;
 };
+
+// Everything a role needs to know about one work item.
+struct Item {
+    int chan, bi, bj, n_in, K;
+    int cpt, lg_npad, n_chan;  // channel packing: cpt channels of 128 / cpt rows (2^lg_npad) each
+    long long B;
+    const CUtensorMap *tm;
+    void *acc;
+};
+
+__device__ __forceinline__ void decode(long long item, int n_tiles, int &chan, int &bi, int &bj);
+
+__device__ __forceinline__ Item get_item(const TParams &p, const CUtensorMap *tmap, long long it) {
+    Item r;
+    if (p.batch) {
+        const int4 e = p.items[p.cta_off[blockIdx.x] + it];
+        const SubDesc &sd = p.subs[e.x];
+        r.chan = e.y;
+        r.bi = e.z & 0xffff;
+        r.bj = e.z >> 16;
+        r.n_in = sd.n_in;
+        r.K = sd.K;
+        r.B = sd.B;
+        r.tm = p.tmaps + e.x;
+        r.acc = sd.acc;
+        r.cpt = sd.cpt;
+        r.lg_npad = sd.cpt == 1 ? 7 : (sd.cpt == 2 ? 6 : 5);
+        r.n_chan = sd.n_chan;
+    } else {
+        decode(blockIdx.x + it * gridDim.x, p.n_tiles, r.chan, r.bi, r.bj);
+        r.n_in = p.n_in;
+        r.K = p.K;
+        r.B = p.B;
+        r.tm = tmap;
+        r.acc = p.acc;
+        r.cpt = 1;
+        r.lg_npad = 7;
+        r.n_chan = 0x7fffffff;
+    }
+    return r;
+}
 
 __device__ __forceinline__ void decode(long long item, int n_tiles, int &chan, int &bi, int &bj) {
     chan = (int)(item / n_tiles);
@@ -113,7 +163,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
         tc::mbar_init(drain_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        tc::prefetch_tmap(&tmap);
+        if (!p.batch) tc::prefetch_tmap(&tmap);
     }
     if (warp == 1) {
         tc::tmem_alloc(tc::smem_u32(tmem_slot), 512);
@@ -123,20 +173,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int nkb = (p.K + KB - 1) / KB;
-    const long long my_items = (p.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const long long my_items = p.batch ? (long long)(p.cta_off[blockIdx.x + 1] - p.cta_off[blockIdx.x])
+                                       : (p.n_items - blockIdx.x + gridDim.x - 1) / gridDim.x;
     // accumulator hand-offs: INT8 one per 512-spectrum chunk, FP16 one per tile
-    const int chunks_per_item = MODE == kInt8 ? (nkb + CHUNK_KB - 1) / CHUNK_KB : 1;
-    const int chunk_kb = MODE == kInt8 ? CHUNK_KB : nkb;
 
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
             long long n = 0;
             for (long long it = 0; it < my_items; ++it) {
-                int chan, bi, bj;
-                decode(blockIdx.x + it * gridDim.x, p.n_tiles, chan, bi, bj);
+                const Item itm = get_item(p, &tmap, it);
+                const int chan = itm.chan, bi = itm.bi, bj = itm.bj;
                 const bool diag = bi == bj;
+                const int nkb = (itm.K + KB - 1) / KB;
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++n) {
                     const int slot = (int)(n % NSTAGE);
@@ -145,12 +194,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                         break;
                     }
                     const uint32_t st = sbase + slot * STAGE_BYTES;
-                    tc::mbar_arrive_expect_tx(full_bar(slot), (diag ? NPL : 2 * NPL) * PLANE);
                     const int s0 = kb * KB;
+                    if (itm.cpt == 1) {
+                        tc::mbar_arrive_expect_tx(full_bar(slot), (diag ? NPL : 2 * NPL) * PLANE);
 #pragma unroll
-                    for (int pl = 0; pl < NPL; ++pl) {
-                        tc::tma_load_4d(st + (NPL + pl) * PLANE, &tmap, s0, bj * TILE, pl, chan, full_bar(slot));
-                        if (!diag) tc::tma_load_4d(st + pl * PLANE, &tmap, s0, bi * TILE, pl, chan, full_bar(slot));
+                        for (int pl = 0; pl < NPL; ++pl) {
+                            tc::tma_load_4d(st + (NPL + pl) * PLANE, itm.tm, s0, bj * TILE, pl, chan, full_bar(slot));
+                            if (!diag) tc::tma_load_4d(st + pl * PLANE, itm.tm, s0, bi * TILE, pl, chan, full_bar(slot));
+                        }
+                    } else {
+                        // packed small sub-array: cpt channels stacked in one diagonal tile,
+                        // each a box of 128 / cpt rows (the tensor map's box height)
+                        const int nv = min(itm.cpt, itm.n_chan - chan);
+                        const int npad = 1 << itm.lg_npad;
+                        tc::mbar_arrive_expect_tx(full_bar(slot), NPL * nv * npad * KB * 2);
+                        for (int q = 0; q < nv; ++q)
+#pragma unroll
+                            for (int pl = 0; pl < NPL; ++pl)
+                                tc::tma_load_4d(st + (NPL + pl) * PLANE + q * npad * KB * 2, itm.tm, s0, 0, pl,
+                                                chan + q, full_bar(slot));
                     }
                 }
                 if (!ok) break;
@@ -166,9 +228,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
             long long n = 0, ch = 0;  // stage and accumulator-chunk counters
             bool alive = true;
             for (long long it = 0; it < my_items && alive; ++it) {
-                int chan, bi, bj;
-                decode(blockIdx.x + it * gridDim.x, p.n_tiles, chan, bi, bj);
-                const bool diag = bi == bj;
+                const Item itm = get_item(p, &tmap, it);
+                const bool diag = itm.bi == itm.bj;
+                const int nkb = (itm.K + KB - 1) / KB;
+                const int chunk_kb = MODE == kInt8 ? CHUNK_KB : nkb;
                 uint32_t d_re = 0, d_im = 0;
                 int buf = 0;
                 for (int kb = 0; kb < nkb; ++kb, ++n) {
@@ -233,10 +296,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
         long long ch = 0;
         bool alive = true;
         for (long long it = 0; it < my_items && alive; ++it) {
-            int chan, bi, bj;
-            decode(blockIdx.x + it * gridDim.x, p.n_tiles, chan, bi, bj);
-            const int I0 = bi * TILE, J0 = bj * TILE;
+            const Item itm = get_item(p, &tmap, it);
+            const int chan = itm.chan;
+            const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
             const int i = I0 + m;
+            const int nkb = (itm.K + KB - 1) / KB;
+            const int chunks_per_item = MODE == kInt8 ? (nkb + CHUNK_KB - 1) / CHUNK_KB : 1;
             if constexpr (MODE == kInt8) {
                 int R[128];  // INT32 sums: Re of j = J0 + 64h + x in R[x], Im in R[64 + x]
 #pragma unroll
@@ -266,7 +331,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                 // write the tile's INT32 sums through a per-warp shared-memory slice so that
                 // every global row segment is written (or read-modify-written) contiguously
                 unsigned char *ostg = sgen + OFF_OSTG + ew * OSTG_WARP;
-                const long long rbase = (long long)chan * p.B;
+                const long long rbase = (long long)chan * itm.B;
                 if (p.vis64) {
                     // 8 double2 per row slice: 32 rows x 128 B
                     double2 *sl = reinterpret_cast<double2 *>(ostg);
@@ -283,7 +348,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                         for (int rr = 0; rr < 8; ++rr) {
                             const int r = rr * 4 + (lane >> 3), e = lane & 7;
                             const int ii = I0 + wq * 32 + r, jj = J0 + 64 * h + 8 * sc + e;
-                            o[rr] = (ii < p.n_in && jj <= ii)
+                            o[rr] = (ii < itm.n_in && jj <= ii)
                                         ? __ldcg(p.vis64 + rbase + (long long)ii * (ii + 1) / 2 + jj)
                                         : make_double2(0.0, 0.0);
                         }
@@ -292,7 +357,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                             const int r = rr * 4 + (lane >> 3), e = lane & 7;
                             const int ii = I0 + wq * 32 + r, jj = J0 + 64 * h + 8 * sc + e;
                             const double2 v = sl[r * 8 + ((e + r) & 7)];
-                            if (ii < p.n_in && jj <= ii)
+                            if (ii < itm.n_in && jj <= ii)
                                 p.vis64[rbase + (long long)ii * (ii + 1) / 2 + jj] =
                                     make_double2(o[rr].x + v.x, o[rr].y + v.y);
                         }
@@ -301,7 +366,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                 } else {
                     // 16 int2 per row slice: 32 rows x 128 B
                     int2 *sl = reinterpret_cast<int2 *>(ostg);
-                    int2 *acc = static_cast<int2 *>(p.acc);
+                    int2 *acc = static_cast<int2 *>(itm.acc);
 #pragma unroll
                     for (int sc = 0; sc < 4; ++sc) {
 #pragma unroll
@@ -311,9 +376,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
 #pragma unroll
                         for (int rr = 0; rr < 16; ++rr) {
                             const int r = rr * 2 + (lane >> 4), e = lane & 15;
-                            const int ii = I0 + wq * 32 + r, jj = J0 + 64 * h + 16 * sc + e;
-                            if (ii < p.n_in && jj <= ii) {
-                                int2 *dst = acc + rbase + (long long)ii * (ii + 1) / 2 + jj;
+                            // tile row / column -> (channel, input) through the channel packing
+                            const int tr = wq * 32 + r, tcl = 64 * h + 16 * sc + e;
+                            const int q = tr >> itm.lg_npad, qc = tcl >> itm.lg_npad;
+                            const int msk = (1 << itm.lg_npad) - 1;
+                            const int ii = I0 + (tr & msk), jj = J0 + (tcl & msk);
+                            if (q == qc && chan + q < itm.n_chan && ii < itm.n_in && jj <= ii) {
+                                int2 *dst = acc + rbase + (long long)q * itm.B + (long long)ii * (ii + 1) / 2 + jj;
                                 int2 v = sl[r * 16 + ((e + r) & 15)];
                                 if (!p.store) {
                                     const int2 o = *dst;
@@ -333,15 +402,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                 tc::tc_fence_after();
                 const uint32_t d = tmem + lane_off + (uint32_t)(buf * 256) + (uint32_t)(64 * h);
                 float2 gi = make_float2(1.f, 0.f);
-                if (p.gains && i < p.n_in) gi = __ldg(p.gains + i);
-                float2 *row = static_cast<float2 *>(p.acc) + (size_t)chan * p.B + (size_t)i * (i + 1) / 2;
+                if (p.gains && i < itm.n_in) gi = __ldg(p.gains + i);
+                float2 *row = static_cast<float2 *>(itm.acc) + (size_t)chan * itm.B + (size_t)i * (i + 1) / 2;
 #pragma unroll 1
                 for (int cb = 0; cb < 4; ++cb) {
                     uint32_t re[16], im[16];
                     tc::tmem_ld16(d + 16u * cb, re);
                     tc::tmem_ld16(d + 128u + 16u * cb, im);
                     tc::tmem_wait_ld();
-                    if (i < p.n_in) {
+                    if (i < itm.n_in) {
 #pragma unroll
                         for (int x = 0; x < 16; ++x) {
                             const int j = J0 + 64 * h + 16 * cb + x;
@@ -353,7 +422,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                                     v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
                                 }
                                 if (p.vis64) {
-                                    double2 *r64 = p.vis64 + (size_t)chan * p.B + (size_t)i * (i + 1) / 2;
+                                    double2 *r64 = p.vis64 + (size_t)chan * itm.B + (size_t)i * (i + 1) / 2;
                                     double2 o = r64[j];
                                     o.x += (double)v.x;
                                     o.y += (double)v.y;
@@ -406,6 +475,44 @@ EncodeTiledFn encode_fn() {
 
 bool xengine_tma_supported(const Handle &h) { return (h.n_spectra % 8) == 0 && encode_fn() != nullptr; }
 
+corr_status tma_encode_planar(void *tmap128, const void *planes, int n_in, int n_chan, int K, int npl,
+                              int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        set_error_text("cuTensorMapEncodeTiled is not available from the driver");
+        return CORR_EUNSUPPORTED;
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)n_in, (cuuint64_t)npl, (cuuint64_t)n_chan};
+    const cuuint64_t strides[3] = {(cuuint64_t)K * 2, (cuuint64_t)K * 2 * n_in, (cuuint64_t)K * 2 * n_in * npl};
+    const cuuint32_t box[4] = {64, (cuuint32_t)box_rows, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(static_cast<CUtensorMap *>(tmap128), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(planes),
+                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error_text("cuTensorMapEncodeTiled rejected a planar layout");
+        return CORR_EINVAL;
+    }
+    return CORR_OK;
+}
+
+corr_status launch_xengine_tma_batch(const void *d_tmaps, const BatchSub *d_subs, const int4 *d_items,
+                                     const int *d_cta_off, int grid, int *status, cudaStream_t st) {
+    using C = TCfg<2, 64>;
+    TParams p{};
+    p.tmaps = static_cast<const CUtensorMap *>(d_tmaps);
+    p.subs = d_subs;
+    p.items = d_items;
+    p.cta_off = d_cta_off;
+    p.batch = 1;
+    p.status = status;
+    p.store = 1;
+    CUtensorMap dummy{};  // unused in batched mode (each item names its sub's map)
+    CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+    k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(dummy, p);
+    return check_launch("k_xeng_tma (batched)");
+}
+
 corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
                                cudaStream_t st) {
     EncodeTiledFn enc = encode_fn();
@@ -429,7 +536,7 @@ corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, con
         set_error_text("cuTensorMapEncodeTiled rejected the planar layout");
         return CORR_EINVAL;
     }
-    TParams p;
+    TParams p{};
     p.acc = h.acc;
     p.vis64 = (h.flags & CORR_FLAG_FUSED_DUMP) ? h.vis64 : nullptr;
     p.gains = gains;
