@@ -176,6 +176,21 @@ CORR_API corr_status corr_get_accum(corr_t *h, void *out, void *stream);
  * ([n_chan][B] complex double, device). Asynchronous. */
 CORR_API corr_status corr_dump(corr_t *h, double *vis_out, void *stream);
 
+/* The whole step from host memory: raw voltages in, FP64 visibilities out, with
+ * the host<->device copies pipelined against the kernels on two library-owned copy
+ * streams (8 input blocks: copy-in overlaps the F-engine; 8 channel blocks:
+ * X-engine and dump overlap the copy-out of the previous block).
+ *   volt_host  [n_in][n_spectra * n_chan] complex int8, host (page-locked memory
+ *              lets the copies run asynchronously)
+ *   chan_scale [n_chan] float, device (see corr_fengine)
+ *   vis_host   [n_chan][B] complex double, host: receives the FP64 long-integration
+ *              buffer after this integration has been added to it (as corr_dump)
+ * INT8 with CORR_FLAG_PLANAR only (CORR_EUNSUPPORTED otherwise). The first call
+ * allocates device copies of the inputs and of the channelised data. Ordered on
+ * `stream`: the call's work is complete when `stream` reaches this point. */
+CORR_API corr_status corr_fx_host(corr_t *h, const void *volt_host, const float *chan_scale, double *vis_host,
+                                  void *stream);
+
 /* Read and clear the handle's device status word. Returns CORR_ETIMEOUT (or
  * another CORR_* code) if a kernel of this handle gave up early since the last
  * check, CORR_OK otherwise. Synchronises `stream`. */

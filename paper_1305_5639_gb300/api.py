@@ -74,6 +74,17 @@ def corr_fengine_power_noalloc(volt, n_in: int, n_chan: int, n_spectra: int, pre
                                                  _stream(stream)), "corr_fengine_power_noalloc")
 
 
+def _hptr(t):
+    if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous():
+        raise ValueError("corr_fx_host takes contiguous host tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def corr_fx_host(h, volt_host, chan_scale, vis_host, stream=None) -> None:
+    check(_lib.load().corr_fx_host(h, _hptr(volt_host), _ptr(chan_scale), _hptr(vis_host), _stream(stream)),
+          "corr_fx_host")
+
+
 def corr_xengine(h, chan_in, gains=None, stream=None) -> None:
     check(_lib.load().corr_xengine(h, _ptr(chan_in), _ptr(gains), _stream(stream)), "corr_xengine")
 
@@ -152,6 +163,10 @@ class Correlator:
 
     def xengine(self, chan_in, gains=None, stream=None):
         corr_xengine(self.h, chan_in, gains, stream)
+
+    def fx_host(self, volt_host, chan_scale, vis_host, stream=None):
+        """Whole step from host buffers (pipelined copies); see corr_fx_host."""
+        corr_fx_host(self.h, volt_host, chan_scale, vis_host, stream)
 
     def accum(self, out=None, stream=None):
         out = self.accum_buffer() if out is None else out

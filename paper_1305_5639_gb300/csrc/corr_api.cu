@@ -2,6 +2,7 @@
 // ownership and kernel dispatch. Every entry point returns a status code.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -55,6 +56,16 @@ void free_buffers(Handle &h) {
     cudaFree(h.bwd_ws);
     cudaFree(h.planar_ws);
     h.planar_ws = nullptr;
+    cudaFree(h.fx_volt);
+    cudaFree(h.fx_chan);
+    h.fx_volt = h.fx_chan = nullptr;
+    if (h.fx_in) cudaStreamDestroy(h.fx_in);
+    if (h.fx_out) cudaStreamDestroy(h.fx_out);
+    h.fx_in = h.fx_out = nullptr;
+    for (cudaEvent_t &e : h.fx_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
     h.acc = nullptr;
     h.vis64 = nullptr;
     h.twiddle = nullptr;
@@ -294,6 +305,69 @@ corr_status corr_dump(corr_t *c, double *vis_out, void *stream) {
         CORR_CUDA_TRY(cudaMemcpyAsync(vis_out, h.vis64, (size_t)h.n_chan * h.n_base * sizeof(double2),
                                       cudaMemcpyDeviceToDevice, st));
     }
+    return CORR_OK;
+}
+
+corr_status corr_fx_host(corr_t *c, const void *volt_host, const float *chan_scale, double *vis_host, void *stream) {
+    if (!c || !volt_host || !chan_scale || !vis_host) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (h.precision != CORR_PREC_INT8 || !(h.flags & CORR_FLAG_PLANAR) || !corr::fengine_supported(h.n_chan))
+        return CORR_EUNSUPPORTED;
+    corr::DeviceGuard dg(h.device);
+    cudaStream_t st = corr::as_stream(stream);
+    constexpr int NB = 8, NC = 8;  // input blocks (copy-in || F-engine), channel blocks (X + dump || copy-out)
+    const size_t volt_bytes = (size_t)h.n_in * h.n_spectra * h.n_chan * 2;
+    const size_t chan_bytes = (size_t)h.n_chan * 2 * h.n_in * h.n_spectra * 2;
+    if (!h.fx_volt) {
+        bool ok = cudaMalloc(&h.fx_volt, volt_bytes) == cudaSuccess && cudaMalloc(&h.fx_chan, chan_bytes) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h.fx_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h.fx_out, cudaStreamNonBlocking) == cudaSuccess;
+        for (cudaEvent_t &e : h.fx_ev)
+            ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return CORR_ENOMEM;
+        }
+    }
+    // ev[0]: start; ev[1..NB]: input block b copied; ev[NB+1..NB+NC]: channel block dumped;
+    // ev[NB+NC+1]: all copies out done
+    cudaEvent_t *ev = h.fx_ev;
+    CORR_CUDA_TRY(cudaEventRecord(ev[0], st));
+    CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_in, ev[0], 0));
+    const size_t row = (size_t)h.n_spectra * h.n_chan * 2;  // bytes of one input's time series
+    const int ib = (h.n_in + NB - 1) / NB;
+    for (int b = 0; b < NB; ++b) {
+        const int i0 = b * ib, i1 = std::min(h.n_in, i0 + ib);
+        if (i1 > i0) {
+            CORR_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(h.fx_volt) + row * i0,
+                                          static_cast<const char *>(volt_host) + row * i0, row * (i1 - i0),
+                                          cudaMemcpyHostToDevice, h.fx_in));
+        }
+        CORR_CUDA_TRY(cudaEventRecord(ev[1 + b], h.fx_in));
+        CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + b], 0));
+        corr_status s = corr::launch_fengine_range(h, h.fx_volt, chan_scale, h.fx_chan, i0, i1 - i0, st);
+        if (s != CORR_OK) return s;
+    }
+    const bool fused = (h.flags & CORR_FLAG_FUSED_DUMP) != 0;
+    const bool store = h.acc_zero;
+    const int cb = (h.n_chan + NC - 1) / NC;
+    for (int k = 0; k < NC; ++k) {
+        const int c0 = k * cb, c1 = std::min(h.n_chan, c0 + cb);
+        corr_status s = corr::launch_xengine_tma_range(h, h.fx_chan, 2, nullptr, store, c0, c1, st);
+        if (s == CORR_OK && !fused) s = corr::launch_dump_range(h, c0, c1, st);
+        if (s != CORR_OK) return s;
+        CORR_CUDA_TRY(cudaEventRecord(ev[1 + NB + k], st));
+        CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_out, ev[1 + NB + k], 0));
+        if (c1 > c0) {
+            const size_t off = (size_t)c0 * h.n_base;
+            CORR_CUDA_TRY(cudaMemcpyAsync(vis_host + 2 * off, h.vis64 + off, sizeof(double2) * (size_t)(c1 - c0) * h.n_base,
+                                          cudaMemcpyDeviceToHost, h.fx_out));
+        }
+    }
+    CORR_CUDA_TRY(cudaEventRecord(ev[1 + NB + NC], h.fx_out));
+    CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + NB + NC], 0));
+    h.acc_zero = true;
+    h.acc_spectra = 0;
     return CORR_OK;
 }
 

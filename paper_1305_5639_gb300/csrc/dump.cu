@@ -23,16 +23,19 @@ __global__ void __launch_bounds__(256) k_dump(AccT *__restrict__ acc, double2 *_
 
 }  // namespace
 
-corr_status launch_dump(const Handle &h, cudaStream_t st) {
-    const long long n = (long long)h.n_chan * h.n_base;
-    if (n == 0) return CORR_OK;
+corr_status launch_dump(const Handle &h, cudaStream_t st) { return launch_dump_range(h, 0, h.n_chan, st); }
+
+corr_status launch_dump_range(const Handle &h, int c0, int c1, cudaStream_t st) {
+    const long long n = (long long)(c1 - c0) * h.n_base;
+    if (n <= 0) return CORR_OK;
+    const long long off = (long long)c0 * h.n_base;
     long long blocks = (n + 255) / 256;
     const long long cap = (long long)h.n_sm * 16;
     if (blocks > cap) blocks = cap;
     if (h.precision == CORR_PREC_INT8)
-        k_dump<int2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<int2 *>(h.acc), h.vis64, n);
+        k_dump<int2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<int2 *>(h.acc) + off, h.vis64 + off, n);
     else
-        k_dump<float2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<float2 *>(h.acc), h.vis64, n);
+        k_dump<float2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<float2 *>(h.acc) + off, h.vis64 + off, n);
     return check_launch("k_dump");
 }
 

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant && MO
                                                       const float *__restrict__ scale,
                                                       void *__restrict__ out,
                                                       double *__restrict__ power, int n_in, int K,
-                                                      const float2 *__restrict__ tw_glob) {
+                                                      const float2 *__restrict__ tw_glob, int i0) {
     using C = FCfg<N, I8, MODE>;
     constexpr int T = C::T, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant && MO
     float *scs = reinterpret_cast<float *>(smem_raw + C::ex_bytes);                  // [N] (power)
     uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::ex_bytes + C::pw_bytes);  // staging
 
-    const int i = blockIdx.y;
+    const int i = i0 + blockIdx.y;
     const int a0 = blockIdx.x * SB;
     if constexpr (MODE == kPower) {
         for (int m = threadIdx.x; m < N; m += kThreads) scs[m] = 0.0f;
@@ -248,6 +248,7 @@ struct FShape {
     int n_in, n_chan, n_spectra;
     bool i8;
     const float2 *tw;  // [k1][t] table for n_chan = T x T
+    int i0 = 0, n_run = -1;  // inputs [i0, i0 + n_run) of the n_in (n_run < 0: all)
 };
 
 template <int N, bool I8, int MODE>
@@ -256,8 +257,8 @@ corr_status launch_one(const FShape &f, const void *volt, const float *scale, vo
     using C = FCfg<N, I8, MODE>;
     auto kern = k_fengine<N, I8, MODE>;
     CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-    dim3 grid((f.n_spectra + C::SB - 1) / C::SB, f.n_in);
-    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw);
+    dim3 grid((f.n_spectra + C::SB - 1) / C::SB, f.n_run < 0 ? f.n_in : f.n_run);
+    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw, f.i0);
     return check_launch("k_fengine");
 }
 
@@ -307,6 +308,18 @@ corr_status launch_fengine(const Handle &h, const void *volt, const float *scale
         return dispatch<kRequantPlanar>(shape_of(h), volt, scale, out, nullptr, st);
     if (h.precision == CORR_PREC_INT8) return dispatch<kRequant>(shape_of(h), volt, scale, out, nullptr, st);
     return dispatch<kFloatOut>(shape_of(h), volt, nullptr, out, nullptr, st);
+}
+
+corr_status launch_fengine_range(const Handle &h, const void *volt, const float *scale, void *out, int i0, int n_run,
+                                 cudaStream_t st) {
+    FShape f = shape_of(h);
+    f.i0 = i0;
+    f.n_run = n_run;
+    if (n_run <= 0) return CORR_OK;
+    if (h.precision == CORR_PREC_INT8 && (h.flags & CORR_FLAG_PLANAR))
+        return dispatch<kRequantPlanar>(f, volt, scale, out, nullptr, st);
+    if (h.precision == CORR_PREC_INT8) return dispatch<kRequant>(f, volt, scale, out, nullptr, st);
+    return dispatch<kFloatOut>(f, volt, nullptr, out, nullptr, st);
 }
 
 corr_status launch_fengine_power(const Handle &h, const void *volt, float *power, cudaStream_t st) {

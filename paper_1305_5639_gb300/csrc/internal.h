@@ -26,6 +26,11 @@ struct Handle {
     void *planar_ws = nullptr;   // FP16 operand planes for the FP16 tensor-core paths (first use)
     size_t planar_ws_bytes = 0;
     float2 *bwd_ws = nullptr;    // dg partials for corr_backward (allocated on first use)
+    // host-buffer pipeline (corr_fx_host): device copies of the inputs and the
+    // channelised data, two copy streams and per-block events (first use)
+    void *fx_volt = nullptr, *fx_chan = nullptr;
+    cudaStream_t fx_in = nullptr, fx_out = nullptr;
+    cudaEvent_t fx_ev[40] = {};
     size_t bwd_ws_bytes = 0;
 };
 
@@ -52,6 +57,11 @@ corr_status launch_xengine_cudacore(const Handle &h, const void *chan_in, const 
 corr_status launch_xengine_tc(const Handle &h, const void *chan_in, const float2 *gains, bool store,
                               cudaStream_t st);
 corr_status launch_dump(const Handle &h, cudaStream_t st);
+corr_status launch_dump_range(const Handle &h, int c0, int c1, cudaStream_t st);
+corr_status launch_fengine_range(const Handle &h, const void *volt, const float *scale, void *out, int i0, int n_run,
+                                 cudaStream_t st);
+corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
+                                     int c0, int c1, cudaStream_t st);
 size_t backward_workspace_bytes(const Handle &h);
 corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const float2 *chan_in,
                                const float2 *gains, float2 *grad_chan, float2 *grad_gains, float2 *ws,

@@ -74,6 +74,7 @@ struct TParams {
     const int4 *items;
     const int *cta_off;
     int batch;
+    int c0;  // first channel of a channel-range launch
     const float2 *gains;
     int *status;
     long long B;
@@ -110,6 +111,7 @@ __device__ __forceinline__ Item get_item(const TParams &p, const CUtensorMap *tm
         r.n_chan = sd.n_chan;
     } else {
         decode(blockIdx.x + it * gridDim.x, p.n_tiles, r.chan, r.bi, r.bj);
+        r.chan += p.c0;
         r.n_in = p.n_in;
         r.K = p.K;
         r.B = p.B;
@@ -515,6 +517,12 @@ corr_status launch_xengine_tma_batch(const void *d_tmaps, const BatchSub *d_subs
 
 corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
                                cudaStream_t st) {
+    return launch_xengine_tma_range(h, planes, npl, gains, store, 0, h.n_chan, st);
+}
+
+corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
+                                     int c0, int c1, cudaStream_t st) {
+    if (c1 <= c0) return CORR_OK;
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
         set_error_text("cuTensorMapEncodeTiled is not available from the driver");
@@ -544,7 +552,8 @@ corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, con
     p.B = h.n_base;
     const int nb = (h.n_in + TILE - 1) / TILE;
     p.n_tiles = nb * (nb + 1) / 2;
-    p.n_items = (long long)h.n_chan * p.n_tiles;
+    p.n_items = (long long)(c1 - c0) * p.n_tiles;
+    p.c0 = c0;
     p.n_in = h.n_in;
     p.K = h.n_spectra;
     p.store = store ? 1 : 0;
