@@ -112,6 +112,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_time_and_rate(ms_local: float, units_per_rank: float, steps: int, dist=None):
+    """Whole-job timing for N replicas: the step time is the slowest rank's (max over
+    ranks of the time each spent on its own `steps` steps), and the job's throughput
+    is the units all ranks processed divided by it (weak scaling: every rank
+    correlates its own data; no data-path collective). Returns (ms_per_step, rate)."""
+    ws = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+
+        ws = dist.get_world_size()
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_local = float(t.item())
+    ms_step = ms_local / steps
+    return ms_step, ws * units_per_rank / (ms_step * 1e-3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -261,12 +279,7 @@ def run_ours(args):
     f_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     x_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
     d_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_step = ms / args.steps
-    value = ws * cmac_step / (ms_step * 1e-3)
+    ms_step, value = job_time_and_rate(ms, cmac_step, args.steps, torch.distributed if ws > 1 else None)
 
     # ---- end to end through the C ABI with host buffers: pinned raw voltages in, FP64
     # visibilities out, every step (corr_fx_host pipelines the copies with the engines)
