@@ -38,14 +38,14 @@ struct FCfg {
     static constexpr int G = kThreads / T;  // FFTs in flight per CTA
     static constexpr int EXS = T + 1;       // exchange row stride (floats; Re and Im exchanged in turn)
     // spectra per CTA
-    static constexpr int SB = (MODE == kFloatOut || MODE == kRequantPlanar) ? 8 : 16;
+    static constexpr int SB = MODE == kFloatOut ? 8 : 16;
     static_assert(SB % (G < SB ? G : SB) == 0 || G >= SB, "");
     // staging row stride in 32-bit words
-    // kRequant stages int8 code pairs, kRequantPlanar two planes of FP16 codes
-    // (rows of SB halves); one pad word per row keeps the row writes conflict-free
+    // (both requant modes stage the int8 code pairs; the planar mode expands
+    //  them to FP16 planes while copying out)
     static constexpr int ROWW = (MODE == kRequant || MODE == kRequantPlanar) ? SB / 2 + 1
                                 : (MODE == kFloatOut ? 2 * SB + 2 : 0);
-    static constexpr int NPL = MODE == kRequantPlanar ? 2 : 1;
+    static constexpr int NPL = 1;
     static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * T * EXS;
     static constexpr size_t pw_bytes = MODE == kPower ? sizeof(float) * N : 0;
     static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW * NPL;
@@ -65,15 +65,16 @@ __device__ __forceinline__ uint32_t pack_q(float2 v, float sc) {
     return __byte_perm(__float_as_uint(t.x), __float_as_uint(t.y), 0x0040);
 }
 
-// The same decision as pack_q, returned as the two codes in FP16 (exact for
-// |q| <= 127): Re in the low half, Im in the high half. The half with bits 0x64uu
-// is 1024 + u, and u = q + 128.
-__device__ __forceinline__ uint32_t pack_q_f16(float2 v, float sc) {
-    const uint32_t w = pack_q(v, sc) ^ 0x8080u;
-    uint32_t h = __byte_perm(w, 0x64646464u, 0x5140);
+// Two complex int8 codes [re0 im0 re1 im1] -> FP16 pairs (re0, re1) and (im0, im1),
+// exactly: the half with bits 0x64uu is 1024 + u, and u = code + 128.
+__device__ __forceinline__ void codes_to_f16_planes(uint32_t w, uint32_t &re, uint32_t &im) {
+    const uint32_t u = w ^ 0x80808080u;
+    uint32_t hr = __byte_perm(u, 0x64646464u, 0x4240), hi = __byte_perm(u, 0x64646464u, 0x4341);
     const __half2 k1152 = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));
-    __half2 r = __hsub2(*reinterpret_cast<__half2 *>(&h), k1152);
-    return *reinterpret_cast<uint32_t *>(&r);
+    __half2 r = __hsub2(*reinterpret_cast<__half2 *>(&hr), k1152);
+    __half2 m = __hsub2(*reinterpret_cast<__half2 *>(&hi), k1152);
+    re = *reinterpret_cast<uint32_t *>(&r);
+    im = *reinterpret_cast<uint32_t *>(&m);
 }
 
 // complex int8 sample (16 bits: re in the low byte) -> float2, exactly:
@@ -163,14 +164,9 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant && MO
                 constexpr int k2 = decltype(K2)::value;
                 const int k = t + T * k2;
                 float2 x = v[bitrev(k2, ilog2(T))];
-                if constexpr (MODE == kRequant) {
+                if constexpr (MODE == kRequant || MODE == kRequantPlanar) {
                     uint32_t q = pack_q(x, __ldg(scale + k));
                     reinterpret_cast<uint16_t *>(stg)[(size_t)k * (2 * ROWW) + s] = (uint16_t)q;
-                } else if constexpr (MODE == kRequantPlanar) {
-                    const uint32_t h2 = pack_q_f16(x, __ldg(scale + k));  // FP16 codes, Re low, Im high
-                    uint16_t *sh = reinterpret_cast<uint16_t *>(stg);
-                    sh[(size_t)k * (2 * ROWW) + s] = (uint16_t)(h2 & 0xffffu);
-                    sh[(size_t)(N + k) * (2 * ROWW) + s] = (uint16_t)(h2 >> 16);
                 } else if constexpr (MODE == kFloatOut) {
                     reinterpret_cast<float2 *>(stg)[(size_t)k * (ROWW / 2) + s] = x;
                 } else {
@@ -193,23 +189,30 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant && MO
         // ---- corner turn: row (k, i) gets spectra a0 .. a0 + nv - 1
         const int nv = min(SB, K - a0);
         if constexpr (MODE == kRequantPlanar) {
-            // planar FP16 layout [k][plane][i][a]: one 16-byte row segment (SB = 8 codes) per
-            // (channel, plane); K % 8 == 0 makes every segment 16-byte aligned
-            static_assert(SB == 8, "planar rows are 16 bytes");
+            // planar FP16 layout [k][plane][i][a]: each staged word holds the code
+            // pairs of two spectra, expanded to one FP16 pair per plane
             uint16_t *dst = reinterpret_cast<uint16_t *>(out);
             const uint16_t *sh = reinterpret_cast<const uint16_t *>(stg);
-            if (nv == SB) {
-                for (int row = threadIdx.x; row < 2 * N; row += kThreads) {  // row = plane * N + k
-                    const int pl = row / N, k = row % N;
-                    const uint32_t *w = stg + (size_t)row * ROWW;
-                    const uint4 v = make_uint4(w[0], w[1], w[2], w[3]);
-                    *reinterpret_cast<uint4 *>(dst + (((size_t)k * 2 + pl) * n_in + i) * K + a0) = v;
+            if (nv == SB && (K % 2) == 0) {
+                constexpr int WPR = SB / 2;
+                for (int w = threadIdx.x; w < N * WPR; w += kThreads) {
+                    const int k = w / WPR, c = w % WPR;
+                    uint32_t re, im;
+                    codes_to_f16_planes(stg[(size_t)k * ROWW + c], re, im);
+                    uint16_t *row0 = dst + (((size_t)k * 2) * n_in + i) * K + a0;
+                    reinterpret_cast<uint32_t *>(row0)[c] = re;
+                    reinterpret_cast<uint32_t *>(row0 + (size_t)n_in * K)[c] = im;
                 }
             } else {
-                for (int e = threadIdx.x; e < 2 * N * SB; e += kThreads) {
-                    const int row = e / SB, c = e % SB;
-                    const int pl = row / N, k = row % N;
-                    if (c < nv) dst[(((size_t)k * 2 + pl) * n_in + i) * K + a0 + c] = sh[(size_t)row * (2 * ROWW) + c];
+                for (int e = threadIdx.x; e < N * SB; e += kThreads) {
+                    const int k = e / SB, c = e % SB;
+                    if (c < nv) {
+                        uint32_t re, im;
+                        codes_to_f16_planes((uint32_t)sh[(size_t)k * (2 * ROWW) + c], re, im);
+                        uint16_t *row0 = dst + (((size_t)k * 2) * n_in + i) * K + a0;
+                        row0[c] = (uint16_t)(re & 0xffffu);
+                        row0[(size_t)n_in * K + c] = (uint16_t)(im & 0xffffu);
+                    }
                 }
             }
         } else if constexpr (MODE == kRequant) {
