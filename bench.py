@@ -478,6 +478,72 @@ def run_batched(args):
     return 0
 
 
+def run_calibration(args):
+    """Calibration workload: 512 inputs, 1024 channels, 1024 spectra, per-input
+    complex gains; one gained forward X-engine (FP32 CUDA cores) and one adjoint
+    (dL/dX and dL/dg) per step. Prints the forward, backward and step rates."""
+    import torch
+
+    import synth
+    from paper_1305_5639_gb300 import build as pbuild
+
+    pbuild.build()
+    from paper_1305_5639_gb300 import api
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n_in, N, K = 512, 1024, 1024
+    B = n_in * (n_in + 1) // 2
+    gen = torch.Generator(device=dev).manual_seed(0)
+    X = torch.complex(torch.randn((N, n_in, K), generator=gen, device=dev),
+                      torch.randn((N, n_in, K), generator=gen, device=dev)).contiguous()
+    g = torch.from_numpy(synth.gains(n_in, seed=0)).to(dev)
+    G = torch.complex(torch.randn((N, B), generator=gen, device=dev),
+                      torch.randn((N, B), generator=gen, device=dev)).contiguous() * 1e-6
+    c = api.Correlator(n_in, 1, N, K, precision="fp32")
+    gx = torch.empty_like(X)
+    gg = torch.empty(n_in, dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def fwd():
+        c.xengine(X, g)
+        c.dump(copy=False)
+
+    def bwd():
+        api.corr_backward(c.h, G, X, g, gx, gg)
+
+    for _ in range(args.warmup):
+        fwd()
+        bwd()
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn in (("forward", fwd), ("backward", bwd)):
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / args.steps
+    c.check_status()
+    cm_f, cm_b = N * B * K, N * n_in * n_in * K
+    line = {
+        "metric": METRIC, "value": (cm_f + cm_b) / ((res["forward"] + res["backward"]) * 1e-3), "unit": "cMAC/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["forward"] + res["backward"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "calibration: 512 inputs, 1024 channels, 1024 spectra, complex64, per-input gains; "
+                               "gained X-engine + adjoint (dL/dX, dL/dg)",
+                   "l2": "inputs larger than L2 (4.29 GB)"},
+        "forward_ms": res["forward"], "forward_cmac_per_s": cm_f / (res["forward"] * 1e-3),
+        "backward_ms": res["backward"], "backward_cmac_per_s": cm_b / (res["backward"] * 1e-3),
+        "gpu_launches": 4 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    c.close()
+    return 0
+
+
 def corr_uses_tc(xengine: str) -> bool:
     return xengine in ("auto", "tcgen05")
 
@@ -488,7 +554,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="B", choices=sorted(WORKLOADS) + ["E"])
+    ap.add_argument("--workload", default="B", choices=sorted(WORKLOADS) + ["D", "E"])
     ap.add_argument("--window", type=int, default=16, help="batched workload: channels per sub-array")
     ap.add_argument("--xengine", default="auto", choices=["auto", "cudacore", "tcgen05"])
     ap.add_argument("--layout", default="planar", choices=["planar", "int8"],
@@ -505,6 +571,8 @@ def main():
         return run_reference(args)
     if args.workload == "E":
         return run_batched(args)
+    if args.workload == "D":
+        return run_calibration(args)
     return run_ours(args)
 
 
