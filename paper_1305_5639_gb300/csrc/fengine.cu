@@ -12,6 +12,7 @@
 // A CTA handles one input and SB consecutive spectra; the outputs are staged in
 // shared memory as [channel][spectrum] so that every (channel, input) row segment
 // of SB spectra is written to global memory contiguously (the corner turn).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -36,21 +37,25 @@ struct FCfg {
     static constexpr int T = isqrt_pow4(N);
     static_assert(T * T == N, "N must be a power of 4");
     static constexpr int G = kThreads / T;  // FFTs in flight per CTA
-    static constexpr int EXS = T + 1;       // exchange row stride (floats; Re and Im exchanged in turn)
-    // spectra per CTA
+    // Exchange buffer of one FFT: T rows of EXS floats; row k1 receives Y[0..T-1][k1]
+    // (one column per writing thread) and is read back as float4. EXS and the per-FFT
+    // stride GS keep both the scalar writes and the float4 reads free of bank conflicts:
+    // 4 EXS / 4 odd per quarter warp, and GS = T (mod 32) so that the FFTs sharing a
+    // warp write to disjoint banks.
+    static constexpr int EXS = T == 4 ? 8 : T + 4;
+    static constexpr int GS = T * EXS + (T == 32 ? 0 : T);
     // spectra per CTA: the planar mode writes two planes, so it takes 32 spectra
     // (64-byte row segments) at 2 CTAs/SM; measured 15% faster than 16
     static constexpr int SB = MODE == kFloatOut ? 8 : (MODE == kRequantPlanar ? 32 : 16);
     static_assert(SB % (G < SB ? G : SB) == 0 || G >= SB, "");
-    // staging row stride in 32-bit words
-    // (both requant modes stage the int8 code pairs; the planar mode expands
-    //  them to FP16 planes while copying out)
+    // staging row stride in 32-bit words (odd: the 16-bit code writes of one warp go
+    // to 32 consecutive rows without conflicts); both requant modes stage the int8
+    // code pairs, the planar mode expands them to FP16 planes while copying out
     static constexpr int ROWW = (MODE == kRequant || MODE == kRequantPlanar) ? SB / 2 + 1
                                 : (MODE == kFloatOut ? 2 * SB + 2 : 0);
-    static constexpr int NPL = 1;
-    static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * T * EXS;
+    static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * GS;
     static constexpr size_t pw_bytes = MODE == kPower ? sizeof(float) * N : 0;
-    static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW * NPL;
+    static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW;
     static constexpr size_t smem = ex_bytes + pw_bytes + st_bytes;
 };
 
@@ -58,19 +63,23 @@ struct FCfg {
 // even, the FP32 adder's rounding) and leaves that integer in the low mantissa bits.
 constexpr float kMagic = 12582912.0f;
 
+// Re-pack to int8: q = clamp(rint(S * scale), -127, 127), round half to even.
+// One FMA adds the magic constant M to the product, which rounds it to an integer
+// kept in the low mantissa bits (rint of the exact product); the clamp is then taken
+// on M + q, which is monotonic in the product for every input, so clamping after
+// rounding equals rounding after clamping. The low byte of each result is the code:
+// two's complement (M = 1.5 * 2^23) or offset binary q + 128 (M + 128, OB).
+template <bool OB>
 __device__ __forceinline__ uint32_t pack_q(float2 v, float sc) {
-    // Re-pack to int8: clamp(S * scale) to [-127, 127], round half to even.
-    float2 t = f2_mul(v, make_float2(sc, sc));
-    t = make_float2(fminf(fmaxf(t.x, -127.0f), 127.0f), fminf(fmaxf(t.y, -127.0f), 127.0f));
-    t = f2_add(t, make_float2(kMagic, kMagic));
-    // low byte of each result is the two's-complement int8 code
+    constexpr float M = OB ? kMagic + 128.0f : kMagic;
+    float2 t = f2_fma(v, make_float2(sc, sc), make_float2(M, M));
+    t = make_float2(fminf(fmaxf(t.x, M - 127.0f), M + 127.0f), fminf(fmaxf(t.y, M - 127.0f), M + 127.0f));
     return __byte_perm(__float_as_uint(t.x), __float_as_uint(t.y), 0x0040);
 }
 
-// Two complex int8 codes [re0 im0 re1 im1] -> FP16 pairs (re0, re1) and (im0, im1),
-// exactly: the half with bits 0x64uu is 1024 + u, and u = code + 128.
-__device__ __forceinline__ void codes_to_f16_planes(uint32_t w, uint32_t &re, uint32_t &im) {
-    const uint32_t u = w ^ 0x80808080u;
+// Two complex offset-binary codes [re0 im0 re1 im1] (code = q + 128) -> FP16 pairs
+// (q_re0, q_re1) and (q_im0, q_im1), exactly: the half with bits 0x64uu is 1024 + u.
+__device__ __forceinline__ void ob_codes_to_f16_planes(uint32_t u, uint32_t &re, uint32_t &im) {
     uint32_t hr = __byte_perm(u, 0x64646464u, 0x4240), hi = __byte_perm(u, 0x64646464u, 0x4341);
     const __half2 k1152 = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));
     __half2 r = __hsub2(*reinterpret_cast<__half2 *>(&hr), k1152);
@@ -93,7 +102,7 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
                                                       const float *__restrict__ scale,
                                                       void *__restrict__ out,
                                                       double *__restrict__ power, int n_in, int K,
-                                                      const float2 *__restrict__ tw_glob, int i0) {
+                                                      const float2 *__restrict__ tw_glob, int i0, int vec_out) {
     using C = FCfg<N, I8, MODE>;
     constexpr int T = C::T, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -103,6 +112,16 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
 
     const int i = i0 + blockIdx.y;
     const int a0 = blockIdx.x * SB;
+    {
+        // Warm L2 with this CTA's raw block (SB consecutive spectra of input i, one
+        // contiguous range): the loads of the later spectra then hit L2 instead of HBM.
+        constexpr int BPS = I8 ? 2 : 8;  // bytes per complex sample
+        const int nvs = min(SB, K - a0);
+        const char *blk = reinterpret_cast<const char *>(volt) + ((size_t)i * K + a0) * N * BPS;
+        const int lines = (nvs * N * BPS + 127) / 128;
+        for (int l = threadIdx.x; l < lines; l += kThreads)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + (size_t)l * 128));
+    }
     if constexpr (MODE == kPower) {
         for (int m = threadIdx.x; m < N; m += kThreads) scs[m] = 0.0f;
         __syncthreads();
@@ -110,7 +129,8 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
 
     const int g = threadIdx.x / T;
     const int t = threadIdx.x % T;
-    float *exg = ex + (size_t)g * T * EXS;
+    float *exg = ex + (size_t)g * C::GS;
+    const float4 *exrow = reinterpret_cast<const float4 *>(exg + t * EXS);
     float pw[T];
     if constexpr (MODE == kPower) {
 #pragma unroll
@@ -150,7 +170,10 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
         });
         if constexpr (T <= 32) __syncwarp(); else __syncthreads();
 #pragma unroll
-        for (int tt = 0; tt < T; ++tt) v[tt].x = exg[t * EXS + tt];
+        for (int j = 0; j < T / 4; ++j) {
+            const float4 r = exrow[j];
+            v[4 * j].x = r.x, v[4 * j + 1].x = r.y, v[4 * j + 2].x = r.z, v[4 * j + 3].x = r.w;
+        }
         if constexpr (T <= 32) __syncwarp(); else __syncthreads();
         sfor<0, T>([&](auto K1) {
             constexpr int k1 = decltype(K1)::value;
@@ -158,7 +181,10 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
         });
         if constexpr (T <= 32) __syncwarp(); else __syncthreads();
 #pragma unroll
-        for (int tt = 0; tt < T; ++tt) v[tt].y = exg[t * EXS + tt];
+        for (int j = 0; j < T / 4; ++j) {
+            const float4 r = exrow[j];
+            v[4 * j].y = r.x, v[4 * j + 1].y = r.y, v[4 * j + 2].y = r.z, v[4 * j + 3].y = r.w;
+        }
         if constexpr (T <= 32) __syncwarp(); else __syncthreads();
         fft_dif<T>(v);  // v[bitrev(k2)] = X[t + T k2]
         if (valid) {
@@ -167,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
                 const int k = t + T * k2;
                 float2 x = v[bitrev(k2, ilog2(T))];
                 if constexpr (MODE == kRequant || MODE == kRequantPlanar) {
-                    uint32_t q = pack_q(x, __ldg(scale + k));
+                    const uint32_t q = pack_q<MODE == kRequantPlanar>(x, __ldg(scale + k));
                     reinterpret_cast<uint16_t *>(stg)[(size_t)k * (2 * ROWW) + s] = (uint16_t)q;
                 } else if constexpr (MODE == kFloatOut) {
                     reinterpret_cast<float2 *>(stg)[(size_t)k * (ROWW / 2) + s] = x;
@@ -178,60 +204,54 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
         }
     }
 
-    if constexpr (MODE == kPower) {
-        sfor<0, T>([&](auto K2) {
-            constexpr int k2 = decltype(K2)::value;
-            atomicAdd(&scs[t + T * k2], pw[k2]);
-        });
-        __syncthreads();
-        for (int m = threadIdx.x; m < N; m += kThreads) atomicAdd(&power[m], (double)scs[m]);
-        return;
-    } else {
+    if constexpr (MODE != kPower) {
         __syncthreads();
         // ---- corner turn: row (k, i) gets spectra a0 .. a0 + nv - 1
         const int nv = min(SB, K - a0);
-        if constexpr (MODE == kRequantPlanar) {
-            // planar FP16 layout [k][plane][i][a]: each staged word holds the code
-            // pairs of two spectra, expanded to one FP16 pair per plane
+        if constexpr (MODE == kRequantPlanar || MODE == kRequant) {
             uint16_t *dst = reinterpret_cast<uint16_t *>(out);
             const uint16_t *sh = reinterpret_cast<const uint16_t *>(stg);
-            if (nv == SB && (K % 2) == 0) {
-                constexpr int WPR = SB / 2;
-                for (int w = threadIdx.x; w < N * WPR; w += kThreads) {
-                    const int k = w / WPR, c = w % WPR;
-                    uint32_t re, im;
-                    codes_to_f16_planes(stg[(size_t)k * ROWW + c], re, im);
-                    uint16_t *row0 = dst + (((size_t)k * 2) * n_in + i) * K + a0;
-                    reinterpret_cast<uint32_t *>(row0)[c] = re;
-                    reinterpret_cast<uint32_t *>(row0 + (size_t)n_in * K)[c] = im;
+            // planar FP16 layout [k][plane][i][a]; int8 layout [k][i][a] (complex int8)
+            constexpr int PL = MODE == kRequantPlanar ? 2 : 1;
+            if (nv == SB && vec_out) {
+                // each thread moves 8 spectra of one channel row: 4 staged words
+                // (the code pairs of 2 spectra each) -> one 16-byte store per plane
+                constexpr int CPR = SB / 8;          // 8-spectrum chunks per row
+                constexpr int RPI = kThreads / CPR;  // rows per iteration
+                const int q = threadIdx.x % CPR;
+                int k = threadIdx.x / CPR;
+                const uint32_t *src = stg + (size_t)k * ROWW + 4 * q;
+                uint4 *d = reinterpret_cast<uint4 *>(dst + ((size_t)(PL * k) * n_in + i) * K + a0 + 8 * q);
+                const size_t dstep = (size_t)PL * RPI * n_in * K / 8, dplane = (size_t)n_in * K / 8;
+                for (; k < N; k += RPI, src += RPI * ROWW, d += dstep) {
+                    const uint32_t w0 = src[0], w1 = src[1], w2 = src[2], w3 = src[3];
+                    if constexpr (MODE == kRequantPlanar) {
+                        uint4 re, im;
+                        ob_codes_to_f16_planes(w0, re.x, im.x);
+                        ob_codes_to_f16_planes(w1, re.y, im.y);
+                        ob_codes_to_f16_planes(w2, re.z, im.z);
+                        ob_codes_to_f16_planes(w3, re.w, im.w);
+                        d[0] = re;
+                        d[dplane] = im;
+                    } else {
+                        d[0] = make_uint4(w0, w1, w2, w3);
+                    }
                 }
             } else {
                 for (int e = threadIdx.x; e < N * SB; e += kThreads) {
                     const int k = e / SB, c = e % SB;
                     if (c < nv) {
-                        uint32_t re, im;
-                        codes_to_f16_planes((uint32_t)sh[(size_t)k * (2 * ROWW) + c], re, im);
-                        uint16_t *row0 = dst + (((size_t)k * 2) * n_in + i) * K + a0;
-                        row0[c] = (uint16_t)(re & 0xffffu);
-                        row0[(size_t)n_in * K + c] = (uint16_t)(im & 0xffffu);
+                        const uint16_t code = sh[(size_t)k * (2 * ROWW) + c];
+                        uint16_t *row0 = dst + ((size_t)(PL * k) * n_in + i) * K + a0;
+                        if constexpr (MODE == kRequantPlanar) {
+                            uint32_t re, im;
+                            ob_codes_to_f16_planes((uint32_t)code, re, im);
+                            row0[c] = (uint16_t)(re & 0xffffu);
+                            row0[(size_t)n_in * K + c] = (uint16_t)(im & 0xffffu);
+                        } else {
+                            row0[c] = code;
+                        }
                     }
-                }
-            }
-        } else if constexpr (MODE == kRequant) {
-            uint16_t *dst = reinterpret_cast<uint16_t *>(out);
-            const uint16_t *sh = reinterpret_cast<const uint16_t *>(stg);
-            if (nv == SB && (K % 2) == 0) {
-                constexpr int WPR = SB / 2;  // words per row
-                for (int w = threadIdx.x; w < N * WPR; w += kThreads) {
-                    int k = w / WPR, c = w % WPR;
-                    uint32_t val = stg[(size_t)k * ROWW + c];
-                    uint32_t *d = reinterpret_cast<uint32_t *>(dst + ((size_t)k * n_in + i) * K + a0);
-                    d[c] = val;
-                }
-            } else {
-                for (int e = threadIdx.x; e < N * SB; e += kThreads) {
-                    int k = e / SB, c = e % SB;
-                    if (c < nv) dst[((size_t)k * n_in + i) * K + a0 + c] = sh[(size_t)k * (2 * ROWW) + c];
                 }
             }
         } else {
@@ -242,6 +262,15 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
                 if (c < nv) dst[((size_t)k * n_in + i) * K + a0 + c] = sh[(size_t)k * (ROWW / 2) + c];
             }
         }
+    }
+
+    if constexpr (MODE == kPower) {
+        sfor<0, T>([&](auto K2) {
+            constexpr int k2 = decltype(K2)::value;
+            atomicAdd(&scs[t + T * k2], pw[k2]);
+        });
+        __syncthreads();
+        for (int m = threadIdx.x; m < N; m += kThreads) atomicAdd(&power[m], (double)scs[m]);
     }
 }
 
@@ -259,8 +288,12 @@ corr_status launch_one(const FShape &f, const void *volt, const float *scale, vo
     using C = FCfg<N, I8, MODE>;
     auto kern = k_fengine<N, I8, MODE>;
     CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+    // 16-byte row stores need 16-byte aligned rows: an aligned buffer and 8 | n_spectra
+    const int vec_out = (reinterpret_cast<uintptr_t>(out) % 16 == 0) && (f.n_spectra % 8 == 0);
+    // blockIdx.x (the spectra block) varies fastest, so the CTAs resident at one time
+    // write neighbouring segments of the same output rows
     dim3 grid((f.n_spectra + C::SB - 1) / C::SB, f.n_run < 0 ? f.n_in : f.n_run);
-    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw, f.i0);
+    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw, f.i0, vec_out);
     return check_launch("k_fengine");
 }
 

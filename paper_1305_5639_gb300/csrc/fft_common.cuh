@@ -104,6 +104,12 @@ __device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
     return f2_unpack(r);
 }
 
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)), "l"(f2_pack(c)));
+    return f2_unpack(r);
+}
+
 // v * W_L^J with W_L = exp(-j 2 pi / L); trivial factors cost no multiply.
 template <int J, int L>
 __device__ __forceinline__ float2 mul_w(float2 v) {
