@@ -44,19 +44,23 @@ struct FCfg {
     // warp write to disjoint banks.
     static constexpr int EXS = T == 4 ? 8 : T + 4;
     static constexpr int GS = T * EXS + (T == 32 ? 0 : T);
-    // spectra per CTA: the planar mode writes two planes, so it takes 32 spectra
-    // (64-byte row segments) at 2 CTAs/SM; measured 15% faster than 16
-    static constexpr int SB = MODE == kFloatOut ? 8 : (MODE == kRequantPlanar ? 32 : 16);
+    static constexpr bool RQ = MODE == kRequant || MODE == kRequantPlanar;
+    // spectra per CTA: the re-packing modes take 32 (64-byte row segments of the
+    // planar FP16 planes, 2 CTAs/SM at N = 1024)
+    static constexpr int SB = MODE == kFloatOut ? 8 : (RQ ? 32 : 16);
     static_assert(SB % (G < SB ? G : SB) == 0 || G >= SB, "");
-    // staging row stride in 32-bit words (odd: the 16-bit code writes of one warp go
-    // to 32 consecutive rows without conflicts); both requant modes stage the int8
-    // code pairs, the planar mode expands them to FP16 planes while copying out
-    static constexpr int ROWW = (MODE == kRequant || MODE == kRequantPlanar) ? SB / 2 + 1
-                                : (MODE == kFloatOut ? 2 * SB + 2 : 0);
+    // staging row stride in 32-bit words. The re-packing modes stage one 16-bit code
+    // pair per (channel k, spectrum s): a row of SB / 2 = 16 words whose word index is
+    // XOR-swizzled with (k >> 1) & 15, so that the 16-bit writes of one warp (32
+    // consecutive rows) and the 4-word row reads of the copy-out are free of bank
+    // conflicts. The FP32 mode stages float2 values in padded rows.
+    static constexpr int ROWW = RQ ? SB / 2 : (MODE == kFloatOut ? 2 * SB + 2 : 0);
+    static_assert(!RQ || ROWW == 16, "swizzle assumes 16-word rows");
     static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * GS;
     static constexpr size_t pw_bytes = MODE == kPower ? sizeof(float) * N : 0;
+    static constexpr size_t tw_bytes = sizeof(float2) * (size_t)N;  // twiddle table copy
     static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW;
-    static constexpr size_t smem = ex_bytes + pw_bytes + st_bytes;
+    static constexpr size_t smem = ex_bytes + pw_bytes + tw_bytes + st_bytes;
 };
 
 // 1.5 * 2^23: adding it to |v| <= 2^22 rounds v to the nearest integer (ties to
@@ -98,7 +102,7 @@ __device__ __forceinline__ float2 i8_to_f2(uint32_t w) {
 }
 
 template <int N, bool I8, int MODE>
-__global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 : 3) k_fengine(const void *__restrict__ volt,
+__global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const void *__restrict__ volt,
                                                       const float *__restrict__ scale,
                                                       void *__restrict__ out,
                                                       double *__restrict__ power, int n_in, int K,
@@ -108,7 +112,10 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *ex = reinterpret_cast<float *>(smem_raw);                                 // [G][T][EXS]
     float *scs = reinterpret_cast<float *>(smem_raw + C::ex_bytes);                  // [N] (power)
-    uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::ex_bytes + C::pw_bytes);  // staging
+    float2 *tws = reinterpret_cast<float2 *>(smem_raw + C::ex_bytes + C::pw_bytes);  // [k1][t] twiddles
+    uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::ex_bytes + C::pw_bytes + C::tw_bytes);  // staging
+    // 16-bit slot of code (k, s) in the swizzled staging rows
+    auto slot = [](int k, int s) { return k * (2 * ROWW) + 2 * ((s >> 1) ^ ((k >> 1) & 15)) + (s & 1); };
 
     const int i = i0 + blockIdx.y;
     const int a0 = blockIdx.x * SB;
@@ -122,10 +129,13 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
         for (int l = threadIdx.x; l < lines; l += kThreads)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + (size_t)l * 128));
     }
-    if constexpr (MODE == kPower) {
-        for (int m = threadIdx.x; m < N; m += kThreads) scs[m] = 0.0f;
-        __syncthreads();
+    // per-CTA copy of the twiddle table (shared-memory loads in the FFT loop; measured
+    // faster than L1 lookups, while the channel scales are faster from L1)
+    for (int m = threadIdx.x; m < N; m += kThreads) {
+        tws[m] = __ldg(tw_glob + m);
+        if constexpr (MODE == kPower) scs[m] = 0.0f;
     }
+    __syncthreads();
 
     const int g = threadIdx.x / T;
     const int t = threadIdx.x % T;
@@ -160,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
         sfor<0, T>([&](auto K1) {
             constexpr int k1 = decltype(K1)::value;
             // twiddle W_N^(t k1), table laid out [k1][t]
-            if constexpr (k1 != 0) v[bitrev(k1, ilog2(T))] = cmul(v[bitrev(k1, ilog2(T))], __ldg(tw_glob + k1 * T + t));
+            if constexpr (k1 != 0) v[bitrev(k1, ilog2(T))] = cmul(v[bitrev(k1, ilog2(T))], tws[k1 * T + t]);
         });
         // ---- exchange (Re, then Im; the other half stays in place) and pass 2:
         // thread t now plays k1 = t and takes Y[tt][k1]
@@ -194,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
                 float2 x = v[bitrev(k2, ilog2(T))];
                 if constexpr (MODE == kRequant || MODE == kRequantPlanar) {
                     const uint32_t q = pack_q<MODE == kRequantPlanar>(x, __ldg(scale + k));
-                    reinterpret_cast<uint16_t *>(stg)[(size_t)k * (2 * ROWW) + s] = (uint16_t)q;
+                    reinterpret_cast<uint16_t *>(stg)[slot(k, s)] = (uint16_t)q;
                 } else if constexpr (MODE == kFloatOut) {
                     reinterpret_cast<float2 *>(stg)[(size_t)k * (ROWW / 2) + s] = x;
                 } else {
@@ -220,11 +230,16 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
                 constexpr int RPI = kThreads / CPR;  // rows per iteration
                 const int q = threadIdx.x % CPR;
                 int k = threadIdx.x / CPR;
-                const uint32_t *src = stg + (size_t)k * ROWW + 4 * q;
+                // physical words of logical words 4q .. 4q + 3 in row k; the swizzle
+                // (k >> 1) & 15 is the same for k + RPI (RPI / 2 is a multiple of 16)
+                static_assert((RPI / 2) % 16 == 0 || RPI >= N, "");
+                const int h = (k >> 1) & 15;
+                const int o0 = (4 * q) ^ h, o1 = (4 * q + 1) ^ h, o2 = (4 * q + 2) ^ h, o3 = (4 * q + 3) ^ h;
+                const uint32_t *src = stg + (size_t)k * ROWW;
                 uint4 *d = reinterpret_cast<uint4 *>(dst + ((size_t)(PL * k) * n_in + i) * K + a0 + 8 * q);
                 const size_t dstep = (size_t)PL * RPI * n_in * K / 8, dplane = (size_t)n_in * K / 8;
                 for (; k < N; k += RPI, src += RPI * ROWW, d += dstep) {
-                    const uint32_t w0 = src[0], w1 = src[1], w2 = src[2], w3 = src[3];
+                    const uint32_t w0 = src[o0], w1 = src[o1], w2 = src[o2], w3 = src[o3];
                     if constexpr (MODE == kRequantPlanar) {
                         uint4 re, im;
                         ob_codes_to_f16_planes(w0, re.x, im.x);
@@ -241,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, (N >= 1024 && MODE != kRequant) ? 2 
                 for (int e = threadIdx.x; e < N * SB; e += kThreads) {
                     const int k = e / SB, c = e % SB;
                     if (c < nv) {
-                        const uint16_t code = sh[(size_t)k * (2 * ROWW) + c];
+                        const uint16_t code = sh[slot(k, c)];
                         uint16_t *row0 = dst + ((size_t)(PL * k) * n_in + i) * K + a0;
                         if constexpr (MODE == kRequantPlanar) {
                             uint32_t re, im;
