@@ -59,8 +59,8 @@ enum {
     CORR_PREC_FP32 = 0,      /* float input, FP32 CUDA-core FFMA */
     CORR_PREC_INT8 = 1,      /* complex int8 input, exact integer result (INT32) */
     CORR_PREC_FP16 = 2,      /* float input rounded to FP16, FP32 accumulation (tensor cores) */
-    CORR_PREC_FP16_HILO = 3  /* float input split x = h + 2^-11 l into two FP16 parts,
-                                V ~ hh + 2^-11 (hl + lh), FP32 accumulation (tensor cores) */
+    CORR_PREC_FP16_HILO = 3  /* float input split x = h + l into two FP16 parts, h = fp16(x),
+                                l = fp16(x - h); V ~ hh + hl + lh, FP32 accumulation (tensor cores) */
 };
 
 /* X-engine implementation. AUTO picks tcgen05 tensor cores for INT8/FP16/FP16_HILO
@@ -209,8 +209,14 @@ CORR_API corr_status corr_reset(corr_t *h, void *stream);
  *   grad_gains [n_in] complex float or NULL:
  *             dL/dg_m = sum_f sum_j G^_f,mj g_j V_f,jm,
  * with G^ the Hermitian completion of G (G^_ij = G_ij for i > j,
- * G^_ji = conj G_ij, G^_ii = 2 Re G_ii). FP32 precision only (CORR_ESTATE
- * otherwise). */
+ * G^_ji = conj G_ij, G^_ii = 2 Re G_ii).
+ * CORR_PREC_FP32: FP32 CUDA-core GEMM. CORR_PREC_FP16_HILO: the dX GEMM on tcgen05
+ * tensor cores with both operands split into FP16 hi/lo parts; G^ diag(g) is scaled
+ * per channel by an exact power of two into FP16 range, while chan_in is used as
+ * given (its magnitudes should lie in FP16's normal range, 6.1e-5 .. 6.5e4, as for
+ * the FP16 forward paths); needs n_in and n_spectra multiples of 8 (else
+ * CORR_EUNSUPPORTED). Other precisions: CORR_ESTATE. dL/dg is summed in a fixed
+ * order (bit-reproducible). The first call allocates the workspace. */
 CORR_API corr_status corr_backward(corr_t *h, const float *grad_vis, const void *chan_in, const float *gains,
                           float *grad_chan, float *grad_gains, void *stream);
 

@@ -118,12 +118,30 @@ __global__ void __launch_bounds__(NTH) k_adj(const float2 *__restrict__ Gp, cons
     }
 }
 
-__global__ void k_adj_reduce(const float2 *__restrict__ part, float2 *__restrict__ dg, int n_in, long long n_part) {
+// dL/dg = sum of n_part per-row partials, in two fixed-order levels (bit-reproducible):
+// level 1 sums the partials of kRedSplit contiguous ranges in FP64, level 2 the ranges.
+constexpr int kRedSplit = 64;
+
+__global__ void k_adj_reduce1(const float2 *__restrict__ part, double2 *__restrict__ mid, int n_in, long long n_part) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_in) return;
+    const long long per = (n_part + kRedSplit - 1) / kRedSplit;
+    const long long p0 = per * blockIdx.y, p1 = min(n_part, p0 + per);
+    double sr = 0.0, si = 0.0;
+    for (long long q = p0; q < p1; ++q) {
+        const float2 v = __ldg(part + q * n_in + m);
+        sr += v.x;
+        si += v.y;
+    }
+    mid[(size_t)blockIdx.y * n_in + m] = make_double2(sr, si);
+}
+
+__global__ void k_adj_reduce2(const double2 *__restrict__ mid, float2 *__restrict__ dg, int n_in) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n_in) return;
     double sr = 0.0, si = 0.0;
-    for (long long p = 0; p < n_part; ++p) {
-        float2 v = part[p * n_in + m];
+    for (int s = 0; s < kRedSplit; ++s) {
+        const double2 v = mid[(size_t)s * n_in + m];
         sr += v.x;
         si += v.y;
     }
@@ -134,8 +152,10 @@ __global__ void k_adj_reduce(const float2 *__restrict__ part, float2 *__restrict
 
 size_t backward_workspace_bytes(const Handle &h) {
     const int nA = (h.n_spectra + TA - 1) / TA;
-    return sizeof(float2) * (size_t)h.n_chan * nA * h.n_in;
+    return align16(sizeof(float2) * (size_t)h.n_chan * nA * h.n_in) + adj_reduce_scratch_bytes(h.n_in);
 }
+
+size_t adj_reduce_scratch_bytes(int n_in) { return sizeof(double2) * (size_t)kRedSplit * n_in; }
 
 corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const float2 *chan_in,
                                const float2 *gains, float2 *grad_chan, float2 *grad_gains, float2 *ws,
@@ -147,8 +167,20 @@ corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const fl
                                 h.n_spectra, h.n_base);
     corr_status s = check_launch("k_adj");
     if (s != CORR_OK || !grad_gains) return s;
-    k_adj_reduce<<<(h.n_in + 127) / 128, 128, 0, st>>>(ws, grad_gains, h.n_in, (long long)h.n_chan * nA);
-    return check_launch("k_adj_reduce");
+    const long long n_part = (long long)h.n_chan * nA;
+    double2 *scratch = reinterpret_cast<double2 *>(reinterpret_cast<char *>(ws) +
+                                                   align16(sizeof(float2) * (size_t)n_part * h.n_in));
+    return launch_adj_reduce(ws, scratch, grad_gains, h.n_in, n_part, st);
+}
+
+corr_status launch_adj_reduce(const float2 *part, double2 *scratch, float2 *dg, int n_in, long long n_part,
+                              cudaStream_t st) {
+    const unsigned nb = (unsigned)((n_in + 127) / 128);
+    k_adj_reduce1<<<dim3(nb, kRedSplit), 128, 0, st>>>(part, scratch, n_in, n_part);
+    corr_status s = check_launch("k_adj_reduce1");
+    if (s != CORR_OK) return s;
+    k_adj_reduce2<<<nb, 128, 0, st>>>(scratch, dg, n_in);
+    return check_launch("k_adj_reduce2");
 }
 
 }  // namespace corr

@@ -1,0 +1,238 @@
+// Adjoint of the gained X-engine on tcgen05 tensor cores, FP16 hi/lo split
+// (gradient-based gain calibration through Eq. 2 of Section 2).
+//
+// Per channel f, with G^_f the Hermitian completion of the packed gradient G_f
+// (G^_ij = G_ij for i > j, G^_ji = conj G_ij, G^_ii = 2 Re G_ii):
+//     A_f   = 2^e_f G^_f diag(g)                        n_in x n_in
+//     Y_f   = 2^-e_f A_f X_f                            (dX GEMM, tensor cores)
+//     dL/dX_f = diag(conj g) Y_f,   dL/dg_m = sum_f sum_a conj(X_f,ma) Y_f,ma
+// The power-of-two scale e_f brings A_f into FP16's normal range (the packed
+// gradient of a loss over visibilities normalised by the integration length is
+// typically ~1e-6); it is exact and undone in the GEMM epilogue. Both operands are
+// split x = h + l with h = fp16(x), l = fp16(x - h) and the products taken as
+// hh + hl + lh (the X-engine's hi/lo scheme). X_f itself is not rescaled, so the
+// channelised data are expected within FP16's normal range, as for the forward
+// FP16 paths.
+//
+// Passes per block of channels:
+//   k_adj_expo   e_f from max |G_f| and max |g|           reads G once
+//   k_adj_aprep  A_f planes [f][Re_h, Im_h, Re_l, Im_l][m][j]   reads G, writes 8 B / entry
+//   k_adj_bprep  conj(X_f)^T planes [f][4][a][j]           reads X, writes 8 B / sample
+//   k_xeng_tma<kAdj>  GEMM + epilogue (dX, dg partials)
+// then one fixed-order reduction of the dg partials over all channels.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace corr {
+namespace {
+
+constexpr int kTile = 32;  // prep tiles: 32 x 32 entries, 256 threads
+
+__device__ __forceinline__ void split_hl(float x, __half &h, __half &l) {
+    h = __float2half_rn(x);
+    l = __float2half_rn(x - __half2float(h));
+}
+
+// e_f = 15 - k with bound(f) < 2^k, bound = 3 max|G_f| max|g| (>= every |Re|, |Im| of A_f / 2^e_f)
+__global__ void __launch_bounds__(256) k_adj_expo(const float2 *__restrict__ Gp, const float2 *__restrict__ gains,
+                                                  int *__restrict__ expo, int n_in, long long B, int c0) {
+    __shared__ float red[2][8];
+    const float2 *G = Gp + (size_t)(c0 + blockIdx.x) * B;
+    float mg = 0.f, mq = gains ? 0.f : 1.f;
+    for (long long b = threadIdx.x; b < B; b += blockDim.x) {
+        const float2 v = __ldg(G + b);
+        mg = fmaxf(mg, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    if (gains)
+        for (int j = threadIdx.x; j < n_in; j += blockDim.x) {
+            const float2 v = __ldg(gains + j);
+            mq = fmaxf(mq, sqrtf(v.x * v.x + v.y * v.y));
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        mg = fmaxf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+        mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = mg;
+        red[1][threadIdx.x >> 5] = mq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            mg = fmaxf(mg, red[0][w]);
+            mq = fmaxf(mq, red[1][w]);
+        }
+        const float bound = 3.0f * mg * mq;
+        int e = 0;
+        if (bound > 0.f && isfinite(bound)) {
+            int k = 0;
+            frexpf(bound, &k);  // bound < 2^k
+            e = min(100, max(-100, 15 - k));
+        }
+        expo[blockIdx.x] = e;
+    }
+}
+
+// A_f = 2^e_f G^_f diag(g) as four FP16 planes [f - c0][plane][m][j]; one CTA per
+// 32 x 32 tile (rows m, columns j); the packed storage holds only j <= m, so tiles
+// above the diagonal read the mirrored tile and conjugate it.
+__global__ void __launch_bounds__(256) k_adj_aprep(const float2 *__restrict__ Gp, const float2 *__restrict__ gains,
+                                                   const int *__restrict__ expo, __half *__restrict__ A, int n_in,
+                                                   long long B, int c0) {
+    __shared__ float2 T[kTile][kTile + 1];
+    const int mb = blockIdx.y, jb = blockIdx.x, fl = blockIdx.z;
+    const float2 *G = Gp + (size_t)(c0 + fl) * B;
+    const int m0 = mb * kTile, j0 = jb * kTile;
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int r = e / kTile, c = e % kTile;
+        float2 v = make_float2(0.f, 0.f);
+        if (mb > jb) {  // T[r][c] = G(m0 + r, j0 + c)
+            const int m = m0 + r, j = j0 + c;
+            if (m < n_in && j < n_in) v = __ldg(G + (size_t)m * (m + 1) / 2 + j);
+        } else if (mb < jb) {  // T[r][c] = G(j0 + r, m0 + c), the mirrored tile
+            const int j = j0 + r, m = m0 + c;
+            if (j < n_in && m < n_in) v = __ldg(G + (size_t)j * (j + 1) / 2 + m);
+        } else {  // diagonal tile: its lower triangle
+            const int m = m0 + r, j = m0 + c;
+            if (c <= r && m < n_in) v = __ldg(G + (size_t)m * (m + 1) / 2 + j);
+        }
+        T[r][c] = v;
+    }
+    __syncthreads();
+    const float sc = ldexpf(1.0f, __ldg(expo + fl));
+    // each thread: 4 consecutive j of one row m
+    const int r = threadIdx.x / (kTile / 4), c4 = (threadIdx.x % (kTile / 4)) * 4;
+    const int m = m0 + r;
+    if (m >= n_in || j0 + c4 >= n_in) return;
+    __half hv[4][4];  // [plane][q]
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = c4 + q, j = j0 + c;
+        float2 gh;
+        if (mb > jb) gh = T[r][c];
+        else if (mb < jb) gh = make_float2(T[c][r].x, -T[c][r].y);
+        else if (r > c) gh = T[r][c];
+        else if (r < c) gh = make_float2(T[c][r].x, -T[c][r].y);
+        else gh = make_float2(2.0f * T[r][r].x, 0.0f);
+        const float2 g = gains ? __ldg(gains + j) : make_float2(1.f, 0.f);
+        const float zr = (gh.x * g.x - gh.y * g.y) * sc, zi = (gh.x * g.y + gh.y * g.x) * sc;
+        split_hl(zr, hv[0][q], hv[2][q]);
+        split_hl(zi, hv[1][q], hv[3][q]);
+    }
+    const size_t plane = (size_t)n_in * n_in;
+    __half *dst = A + (size_t)fl * 4 * plane + (size_t)m * n_in + j0 + c4;
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl) {
+        uint2 w;
+        w.x = (uint32_t)__half_as_ushort(hv[pl][0]) | ((uint32_t)__half_as_ushort(hv[pl][1]) << 16);
+        w.y = (uint32_t)__half_as_ushort(hv[pl][2]) | ((uint32_t)__half_as_ushort(hv[pl][3]) << 16);
+        *reinterpret_cast<uint2 *>(dst + pl * plane) = w;
+    }
+}
+
+// conj(X_f)^T as four FP16 planes [f - c0][plane][a][j]: one CTA per 32 inputs j x
+// 32 spectra a, transposed through shared memory.
+__global__ void __launch_bounds__(256) k_adj_bprep(const float2 *__restrict__ X, __half *__restrict__ Bt, int n_in,
+                                                   int K, int c0) {
+    __shared__ float2 T[kTile][kTile + 1];  // T[j][a]
+    const int ab = blockIdx.x, jb = blockIdx.y, fl = blockIdx.z;
+    const int j0 = jb * kTile, a0 = ab * kTile;
+    const float2 *Xc = X + (size_t)(c0 + fl) * n_in * K;
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int r = e / kTile, c = e % kTile;
+        const int j = j0 + r, a = a0 + c;
+        T[r][c] = (j < n_in && a < K) ? __ldg(Xc + (size_t)j * K + a) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int r = threadIdx.x / (kTile / 4), c4 = (threadIdx.x % (kTile / 4)) * 4;  // row a, 4 j
+    const int a = a0 + r;
+    if (a >= K || j0 + c4 >= n_in) return;
+    __half hv[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 x = T[c4 + q][r];
+        split_hl(x.x, hv[0][q], hv[2][q]);
+        split_hl(-x.y, hv[1][q], hv[3][q]);
+    }
+    const size_t plane = (size_t)K * n_in;
+    __half *dst = Bt + (size_t)fl * 4 * plane + (size_t)a * n_in + j0 + c4;
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl) {
+        uint2 w;
+        w.x = (uint32_t)__half_as_ushort(hv[pl][0]) | ((uint32_t)__half_as_ushort(hv[pl][1]) << 16);
+        w.y = (uint32_t)__half_as_ushort(hv[pl][2]) | ((uint32_t)__half_as_ushort(hv[pl][3]) << 16);
+        *reinterpret_cast<uint2 *>(dst + pl * plane) = w;
+    }
+}
+
+// Workspace layout: [dg partials][reduce scratch][exponents][A planes][B planes],
+// the planes sized for one block of chan_block channels.
+struct TcWs {
+    size_t part, scratch, expo, a, b, total;
+    int cb;
+};
+
+constexpr size_t kPlaneBudget = (size_t)1 << 30;  // operand planes of one channel block
+
+TcWs tc_layout(const Handle &h) {
+    TcWs w{};
+    const int nbj = (h.n_spectra + 127) / 128;
+    const size_t per_chan = 8ull * h.n_in * h.n_in + 8ull * h.n_spectra * h.n_in;  // A + B planes
+    w.cb = (int)std::max<size_t>(1, std::min<size_t>((size_t)h.n_chan, kPlaneBudget / per_chan));
+    size_t o = 0;
+    w.part = o;
+    o += align16(sizeof(float2) * (size_t)h.n_chan * nbj * 2 * h.n_in);
+    w.scratch = o;
+    o += align16(adj_reduce_scratch_bytes(h.n_in));
+    w.expo = o;
+    o = (o + sizeof(int) * (size_t)h.n_chan + 1023) & ~(size_t)1023;
+    w.a = o;
+    o += align16(8ull * w.cb * h.n_in * h.n_in);
+    o = (o + 1023) & ~(size_t)1023;
+    w.b = o;
+    o += align16(8ull * w.cb * h.n_spectra * h.n_in);
+    w.total = o;
+    return w;
+}
+
+}  // namespace
+
+size_t backward_tc_workspace_bytes(const Handle &h, int *chan_block) {
+    const TcWs w = tc_layout(h);
+    if (chan_block) *chan_block = w.cb;
+    return w.total;
+}
+
+corr_status launch_backward_tc(const Handle &h, const float2 *grad_vis, const float2 *chan_in, const float2 *gains,
+                               float2 *grad_chan, float2 *grad_gains, void *ws, cudaStream_t st) {
+    if ((h.n_in % 8) != 0 || (h.n_spectra % 8) != 0) return CORR_EUNSUPPORTED;
+    if (h.n_chan > 65535) return CORR_EUNSUPPORTED;
+    const TcWs w = tc_layout(h);
+    char *base = static_cast<char *>(ws);
+    float2 *part = grad_gains ? reinterpret_cast<float2 *>(base + w.part) : nullptr;
+    int *expo = reinterpret_cast<int *>(base + w.expo);
+    __half *A = reinterpret_cast<__half *>(base + w.a);
+    __half *Bt = reinterpret_cast<__half *>(base + w.b);
+    const int nt_in = (h.n_in + kTile - 1) / kTile, nt_k = (h.n_spectra + kTile - 1) / kTile;
+    for (int c0 = 0; c0 < h.n_chan; c0 += w.cb) {
+        const int c1 = std::min(h.n_chan, c0 + w.cb), nc = c1 - c0;
+        k_adj_expo<<<nc, 256, 0, st>>>(grad_vis, gains, expo + c0, h.n_in, h.n_base, c0);
+        corr_status s = check_launch("k_adj_expo");
+        if (s != CORR_OK) return s;
+        k_adj_aprep<<<dim3(nt_in, nt_in, nc), 256, 0, st>>>(grad_vis, gains, expo + c0, A, h.n_in, h.n_base, c0);
+        if ((s = check_launch("k_adj_aprep")) != CORR_OK) return s;
+        k_adj_bprep<<<dim3(nt_k, nt_in, nc), 256, 0, st>>>(chan_in, Bt, h.n_in, h.n_spectra, c0);
+        if ((s = check_launch("k_adj_bprep")) != CORR_OK) return s;
+        s = launch_adjoint_tma(h, A, Bt, expo + c0, chan_in, gains, grad_chan, part, c0, c1, st);
+        if (s != CORR_OK) return s;
+    }
+    if (!grad_gains) return CORR_OK;
+    const int nbj = (h.n_spectra + 127) / 128;
+    return launch_adj_reduce(part, reinterpret_cast<double2 *>(base + w.scratch), grad_gains, h.n_in,
+                             (long long)h.n_chan * nbj * 2, st);
+}
+
+}  // namespace corr

@@ -403,10 +403,29 @@ corr_status corr_backward(corr_t *c, const float *grad_vis, const void *chan_in,
                           float *grad_gains, void *stream) {
     if (!c || !grad_vis || !chan_in) return CORR_EINVAL;
     Handle &h = c->h;
-    if (h.precision != CORR_PREC_FP32) return CORR_ESTATE;
+    if (h.precision != CORR_PREC_FP32 && h.precision != CORR_PREC_FP16_HILO) return CORR_ESTATE;
     if (!grad_chan && !grad_gains) return CORR_OK;
     if (!corr::aligned16(chan_in) || (grad_chan && !corr::aligned16(grad_chan))) return CORR_EINVAL;
     corr::DeviceGuard dg(h.device);
+    if (h.precision == CORR_PREC_FP16_HILO) {
+        // tensor cores, FP16 hi/lo split (dX GEMM on tcgen05)
+        if (!corr::xengine_tma_supported(h) || (h.n_in % 8) != 0) return CORR_EUNSUPPORTED;
+        const size_t need = corr::backward_tc_workspace_bytes(h, nullptr);
+        if (h.bwd_ws_bytes < need) {
+            cudaFree(h.bwd_ws);
+            h.bwd_ws = nullptr;
+            h.bwd_ws_bytes = 0;
+            if (cudaMalloc(&h.bwd_ws, need) != cudaSuccess) {
+                cudaGetLastError();
+                return CORR_ENOMEM;
+            }
+            h.bwd_ws_bytes = need;
+        }
+        return corr::launch_backward_tc(h, reinterpret_cast<const float2 *>(grad_vis),
+                                        static_cast<const float2 *>(chan_in), reinterpret_cast<const float2 *>(gains),
+                                        reinterpret_cast<float2 *>(grad_chan), reinterpret_cast<float2 *>(grad_gains),
+                                        h.bwd_ws, corr::as_stream(stream));
+    }
     if (grad_gains) {
         const size_t need = corr::backward_workspace_bytes(h);
         if (h.bwd_ws_bytes < need) {

@@ -25,7 +25,7 @@ struct Handle {
     double *power64 = nullptr;   // [n_chan] scratch for corr_fengine_power
     void *planar_ws = nullptr;   // FP16 operand planes for the FP16 tensor-core paths (first use)
     size_t planar_ws_bytes = 0;
-    float2 *bwd_ws = nullptr;    // dg partials for corr_backward (allocated on first use)
+    float2 *bwd_ws = nullptr;    // corr_backward workspace (dg partials; tensor-core operand planes)
     // host-buffer pipeline (corr_fx_host): device copies of the inputs and the
     // channelised data, two copy streams and per-block events (first use)
     void *fx_volt = nullptr, *fx_chan = nullptr;
@@ -66,6 +66,20 @@ size_t backward_workspace_bytes(const Handle &h);
 corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const float2 *chan_in,
                                const float2 *gains, float2 *grad_chan, float2 *grad_gains, float2 *ws,
                                cudaStream_t st);
+// Tensor-core adjoint (FP16 hi/lo): workspace bytes and channel-block size, the
+// whole backward pass, and its dX GEMM (see adjoint_tc.cu, xengine_tma.cu).
+size_t backward_tc_workspace_bytes(const Handle &h, int *chan_block);
+corr_status launch_backward_tc(const Handle &h, const float2 *grad_vis, const float2 *chan_in, const float2 *gains,
+                               float2 *grad_chan, float2 *grad_gains, void *ws, cudaStream_t st);
+corr_status launch_adjoint_tma(const Handle &h, const void *a_planes, const void *b_planes, const int *expo,
+                               const float2 *X, const float2 *gains, float2 *dX, float2 *part, int c0, int c1,
+                               cudaStream_t st);
+// dL/dg from per-row partials part[p][n_in], p < n_part, summed in a fixed order
+// (scratch: adj_reduce_scratch_bytes(n_in) bytes, 16-byte aligned).
+size_t adj_reduce_scratch_bytes(int n_in);
+inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+corr_status launch_adj_reduce(const float2 *part, double2 *scratch, float2 *dg, int n_in, long long n_part,
+                              cudaStream_t st);
 bool fengine_supported(int n_chan);
 bool xengine_tma_supported(const Handle &h);
 corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,

@@ -23,6 +23,14 @@
 //                the tile's columns and their INT32 sums
 // Every mbarrier wait is bounded; on time-out the CTA records CORR_ETIMEOUT and
 // every role leaves its loop.
+//
+// The same pipeline runs the adjoint's dX GEMM (mode kAdj): Y_f = A_f X_f with
+// A_f = 2^e_f G^_f diag(g) (n_in x n_in) and X_f (n_in x K), on rectangular tiles
+// (128 rows m of A x 128 spectra a), contracting over the input index j. The J side
+// of a stage then comes from a second tensor map holding conj(X_f)^T as planes
+// [chan][plane][a][j], so that the conjugated-product form above gives exactly
+// Re Y = Ar Xr - Ai Xi and Im Y = Ai Xr + Ar Xi. The epilogue scales by 2^-e_f,
+// writes dX = diag(conj g) Y and the partial sums sum_a conj(X_ma) Y_ma of dL/dg.
 #include <cuda.h>
 
 #include <mutex>
@@ -60,7 +68,7 @@ struct TCfg {
     }
 };
 
-enum Mode { kInt8 = 0, kFp16 = 1 };
+enum Mode { kInt8 = 0, kFp16 = 1, kAdj = 2 };
 
 using SubDesc = BatchSub;
 
@@ -80,6 +88,13 @@ struct TParams {
     long long B;
     long long n_items;
     int n_in, K, n_tiles, store;
+    // adjoint (kAdj): rows = inputs m (n_in), columns = spectra a (n_cols), contraction
+    // over j (K = n_in); tiles per channel n_tiles = nbi * nbj
+    int adj, nbj, n_cols, tchan0;  // tchan0: channel coordinate origin of the tensor maps
+    const float2 *X;               // [chan][m][a] forward input (dg partials)
+    float2 *dX;                    // [chan][m][a] or null
+    float2 *part;                  // [(chan * nbj + bj) * 2 + half][n_in] or null
+    const int *expo;               // [chan - tchan0] power-of-two exponent of A's scaling
 };
 
 // Everything a role needs to know about one work item.
@@ -109,6 +124,20 @@ __device__ __forceinline__ Item get_item(const TParams &p, const CUtensorMap *tm
         r.cpt = sd.cpt;
         r.lg_npad = sd.cpt == 1 ? 7 : (sd.cpt == 2 ? 6 : 5);
         r.n_chan = sd.n_chan;
+    } else if (p.adj) {
+        const long long item = blockIdx.x + it * gridDim.x;
+        r.chan = (int)(item / p.n_tiles) + p.c0;
+        const int t = (int)(item % p.n_tiles);
+        r.bi = t / p.nbj;
+        r.bj = t % p.nbj;
+        r.n_in = p.n_in;
+        r.K = p.K;
+        r.B = p.B;
+        r.tm = tmap;
+        r.acc = p.acc;
+        r.cpt = 1;
+        r.lg_npad = 7;
+        r.n_chan = 0x7fffffff;
     } else {
         decode(blockIdx.x + it * gridDim.x, p.n_tiles, r.chan, r.bi, r.bj);
         r.chan += p.c0;
@@ -135,7 +164,8 @@ __device__ __forceinline__ void decode(long long item, int n_tiles, int &chan, i
 }
 
 template <int MODE, class C>
-__global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant__ CUtensorMap tmap, const TParams p) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant__ CUtensorMap tmap,
+                                                          const __grid_constant__ CUtensorMap tmapB, const TParams p) {
     constexpr int KB = C::KB, NPL = C::NPL, PLANE = C::PLANE, STAGE_BYTES = C::STAGE_BYTES;
     constexpr int CHUNK_KB = C::CHUNK_KB, OFF_OSTG = C::OFF_OSTG, OFF_BAR = C::OFF_BAR;
     extern __shared__ unsigned char smem_raw[];
@@ -166,6 +196,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (!p.batch) tc::prefetch_tmap(&tmap);
+        if constexpr (MODE == kAdj) tc::prefetch_tmap(&tmapB);
     }
     if (warp == 1) {
         tc::tmem_alloc(tc::smem_u32(tmem_slot), 512);
@@ -185,8 +216,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
             long long n = 0;
             for (long long it = 0; it < my_items; ++it) {
                 const Item itm = get_item(p, &tmap, it);
-                const int chan = itm.chan, bi = itm.bi, bj = itm.bj;
-                const bool diag = bi == bj;
+                const int chan = itm.chan - p.tchan0, bi = itm.bi, bj = itm.bj;
+                const bool diag = MODE != kAdj && bi == bj;
+                // J side: the same planes as the I side, or conj(X)^T for the adjoint
+                const CUtensorMap *tmj = MODE == kAdj ? &tmapB : itm.tm;
                 const int nkb = (itm.K + KB - 1) / KB;
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++n) {
@@ -201,7 +234,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                         tc::mbar_arrive_expect_tx(full_bar(slot), (diag ? NPL : 2 * NPL) * PLANE);
 #pragma unroll
                         for (int pl = 0; pl < NPL; ++pl) {
-                            tc::tma_load_4d(st + (NPL + pl) * PLANE, itm.tm, s0, bj * TILE, pl, chan, full_bar(slot));
+                            tc::tma_load_4d(st + (NPL + pl) * PLANE, tmj, s0, bj * TILE, pl, chan, full_bar(slot));
                             if (!diag) tc::tma_load_4d(st + pl * PLANE, itm.tm, s0, bi * TILE, pl, chan, full_bar(slot));
                         }
                     } else {
@@ -231,7 +264,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
             bool alive = true;
             for (long long it = 0; it < my_items && alive; ++it) {
                 const Item itm = get_item(p, &tmap, it);
-                const bool diag = itm.bi == itm.bj;
+                const bool diag = MODE != kAdj && itm.bi == itm.bj;
                 const int nkb = (itm.K + KB - 1) / KB;
                 const int chunk_kb = MODE == kInt8 ? CHUNK_KB : nkb;
                 uint32_t d_re = 0, d_im = 0;
@@ -397,6 +430,61 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                         __syncwarp();
                     }
                 }
+            } else if constexpr (MODE == kAdj) {
+                // dX = conj(g_m) Y and sum_a conj(X_ma) Y_ma over this thread's 64 spectra,
+                // Y = 2^-e_f D (rows m = i, columns a = J0 + 64 h + ...)
+                const int buf = (int)(ch & 1);
+                if (!tc::mbar_wait(accf_bar(buf), af_phase[buf], abort_flag, p.status)) break;
+                af_phase[buf] ^= 1u;
+                tc::tc_fence_after();
+                const uint32_t d = tmem + lane_off + (uint32_t)(buf * 256) + (uint32_t)(64 * h);
+                const float sc = ldexpf(1.0f, -__ldg(p.expo + (chan - p.tchan0)));
+                float2 gc = make_float2(1.f, 0.f);  // conj(g_m)
+                if (p.gains && i < itm.n_in) {
+                    const float2 g = __ldg(p.gains + i);
+                    gc = make_float2(g.x, -g.y);
+                }
+                const size_t rowoff = ((size_t)chan * itm.n_in + (size_t)(i < itm.n_in ? i : 0)) * p.n_cols;
+                float pr = 0.f, pi = 0.f;
+#pragma unroll 1
+                for (int cb = 0; cb < 4; ++cb) {
+                    uint32_t re[16], im[16];
+                    tc::tmem_ld16(d + 16u * cb, re);
+                    tc::tmem_ld16(d + 128u + 16u * cb, im);
+                    tc::tmem_wait_ld();
+                    const int a0 = J0 + 64 * h + 16 * cb;
+                    if (i < itm.n_in && a0 + 16 <= p.n_cols) {
+                        // 16 contiguous spectra: 8 x (two complex values in a float4)
+                        const float4 *xr = reinterpret_cast<const float4 *>(p.X + rowoff + a0);
+                        float4 *dr = p.dX ? reinterpret_cast<float4 *>(p.dX + rowoff + a0) : nullptr;
+#pragma unroll
+                        for (int x = 0; x < 8; ++x) {
+                            const float4 xv = __ldg(xr + x);
+                            const float y0r = __uint_as_float(re[2 * x]) * sc, y0i = __uint_as_float(im[2 * x]) * sc;
+                            const float y1r = __uint_as_float(re[2 * x + 1]) * sc, y1i = __uint_as_float(im[2 * x + 1]) * sc;
+                            pr += xv.x * y0r + xv.y * y0i + xv.z * y1r + xv.w * y1i;
+                            pi += xv.x * y0i - xv.y * y0r + xv.z * y1i - xv.w * y1r;
+                            if (dr)
+                                dr[x] = make_float4(gc.x * y0r - gc.y * y0i, gc.x * y0i + gc.y * y0r,
+                                                    gc.x * y1r - gc.y * y1i, gc.x * y1i + gc.y * y1r);
+                        }
+                    } else if (i < itm.n_in) {
+#pragma unroll 1
+                        for (int x = 0; x < 16; ++x) {
+                            if (a0 + x >= p.n_cols) break;
+                            const float2 xv = __ldg(p.X + rowoff + a0 + x);
+                            const float yr = __uint_as_float(re[x]) * sc, yi = __uint_as_float(im[x]) * sc;
+                            pr += xv.x * yr + xv.y * yi;
+                            pi += xv.x * yi - xv.y * yr;
+                            if (p.dX) p.dX[rowoff + a0 + x] = make_float2(gc.x * yr - gc.y * yi, gc.x * yi + gc.y * yr);
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+                tc::mbar_arrive(acce_bar(buf));
+                ++ch;
+                if (p.part && i < itm.n_in)
+                    p.part[((size_t)chan * p.nbj + itm.bj) * 2 * itm.n_in + (size_t)h * itm.n_in + i] = make_float2(pr, pi);
             } else {
                 const int buf = (int)(ch & 1);
                 if (!tc::mbar_wait(accf_bar(buf), af_phase[buf], abort_flag, p.status)) break;
@@ -511,7 +599,7 @@ corr_status launch_xengine_tma_batch(const void *d_tmaps, const BatchSub *d_subs
     p.store = 1;
     CUtensorMap dummy{};  // unused in batched mode (each item names its sub's map)
     CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-    k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(dummy, p);
+    k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(dummy, dummy, p);
     return check_launch("k_xeng_tma (batched)");
 }
 
@@ -561,17 +649,76 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
     if (h.precision == CORR_PREC_INT8) {
         using C = TCfg<2, 64>;
         CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, p);
+        k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
     } else if (npl == 2) {
         using C = TCfg<2, 64>;
         CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, p);
+        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
     } else {
         using C = TCfg<4, 32>;
         CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, p);
+        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
     }
     return check_launch("k_xeng_tma");
+}
+
+// Planar FP16 operand tensor [chan][plane][rows][cols] (cols innermost) with a box
+// of kb columns x 128 rows.
+static corr_status encode_planes(CUtensorMap *tm, const void *planes, int cols, int rows, int npl, int n_chan,
+                                 int kb) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        set_error_text("cuTensorMapEncodeTiled is not available from the driver");
+        return CORR_EUNSUPPORTED;
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)npl, (cuuint64_t)n_chan};
+    const cuuint64_t strides[3] = {(cuuint64_t)cols * 2, (cuuint64_t)cols * 2 * rows,
+                                   (cuuint64_t)cols * 2 * rows * npl};
+    const cuuint32_t box[4] = {(cuuint32_t)kb, TILE, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(planes), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, kb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error_text("cuTensorMapEncodeTiled rejected an operand layout");
+        return CORR_EINVAL;
+    }
+    return CORR_OK;
+}
+
+corr_status launch_adjoint_tma(const Handle &h, const void *a_planes, const void *b_planes, const int *expo,
+                               const float2 *X, const float2 *gains, float2 *dX, float2 *part, int c0, int c1,
+                               cudaStream_t st) {
+    if (c1 <= c0) return CORR_OK;
+    if ((h.n_in % 8) != 0) return CORR_EUNSUPPORTED;
+    using C = TCfg<4, 32>;
+    const int cb = c1 - c0;
+    CUtensorMap ta, tb;
+    corr_status s = encode_planes(&ta, a_planes, h.n_in, h.n_in, 4, cb, C::KB);
+    if (s != CORR_OK) return s;
+    s = encode_planes(&tb, b_planes, h.n_in, h.n_spectra, 4, cb, C::KB);
+    if (s != CORR_OK) return s;
+    TParams p{};
+    p.gains = gains;
+    p.status = h.status;
+    p.adj = 1;
+    p.n_in = h.n_in;
+    p.K = h.n_in;  // contraction over the input index j
+    p.n_cols = h.n_spectra;
+    const int nbi = (h.n_in + TILE - 1) / TILE;
+    p.nbj = (h.n_spectra + TILE - 1) / TILE;
+    p.n_tiles = nbi * p.nbj;
+    p.n_items = (long long)cb * p.n_tiles;
+    p.c0 = c0;
+    p.tchan0 = c0;
+    p.X = X;
+    p.dX = dX;
+    p.part = part;
+    p.expo = expo;
+    const unsigned grid = (unsigned)(p.n_items < h.n_sm ? p.n_items : h.n_sm);
+    CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kAdj, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+    k_xeng_tma<kAdj, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(ta, tb, p);
+    return check_launch("k_xeng_tma (adjoint)");
 }
 
 }  // namespace corr

@@ -9,7 +9,8 @@ INT8 workload (256 antennas x 2 pol, 1024 channels, 4096 spectra):
   * F-engine on the full raw voltages; re-packed codes of sampled channels against
     the oracle's direct DFT and FP32 decision (unique away from rounding ties).
 Adjoint workload (512 inputs, 1024 channels, 1024 spectra): gradients of the full
-launch against the oracle's closed forms on all channels."""
+launch (FP32 CUDA cores and FP16 hi/lo tensor cores) against the oracle's closed
+forms on all channels."""
 import numpy as np
 import pytest
 import torch
@@ -77,7 +78,8 @@ def test_int8_workload_fengine_full_launch(cuda_ok):
 
 
 @pytest.mark.slow
-def test_adjoint_workload_full_launch(cuda_ok):
+@pytest.mark.parametrize("precision", ["fp32", "fp16_hilo"])
+def test_adjoint_workload_full_launch(cuda_ok, precision):
     n_in, n_chan, Kd = 512, 1024, 1024
     X = synth.chan_sources(n_chan, n_in, Kd, n_src=5, seed=0)
     g = synth.gains(n_in, seed=0)
@@ -86,7 +88,7 @@ def test_adjoint_workload_full_launch(cuda_ok):
     L, dX_ref, dg_ref = oracle.loss_and_grads(X, g, M, w)
     Vp = oracle.apply_gains(oracle.cmac(X), g, n_in)
     G = (2.0 * w * (Vp / Kd - M) / Kd).astype(np.complex64)
-    c = api.Correlator(n_in, 1, n_chan, Kd)
+    c = api.Correlator(n_in, 1, n_chan, Kd, precision=precision)
     dX, dg = c.backward(torch.from_numpy(G).to(DEV), torch.from_numpy(X).to(DEV), torch.from_numpy(g).to(DEV))
     c.check_status()
     dX = dX.cpu().numpy()
