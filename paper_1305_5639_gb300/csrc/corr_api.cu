@@ -329,11 +329,13 @@ corr_status corr_fx_host(corr_t *c, const void *volt_host, const float *chan_sca
             return CORR_ENOMEM;
         }
     }
-    // ev[0]: start; ev[1..NB]: input block b copied; ev[NB+1..NB+NC]: channel block dumped;
-    // ev[NB+NC+1]: all copies out done
+    // ev[1..NB]: input block b copied; ev[NB+1..NB+NC]: channel block dumped;
+    // ev[NB+NC+1]: all copies out done; ev[NB+NC+2]: the F-engine has read the device
+    // copy of the inputs (recorded by the previous call). The copy-in waits only for
+    // that, not for `stream`, so that it overlaps the previous call's X-engine and
+    // copy-out when calls are issued back to back.
     cudaEvent_t *ev = h.fx_ev;
-    CORR_CUDA_TRY(cudaEventRecord(ev[0], st));
-    CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_in, ev[0], 0));
+    CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_in, ev[NB + NC + 2], 0));
     const size_t row = (size_t)h.n_spectra * h.n_chan * 2;  // bytes of one input's time series
     const int ib = (h.n_in + NB - 1) / NB;
     for (int b = 0; b < NB; ++b) {
@@ -348,6 +350,7 @@ corr_status corr_fx_host(corr_t *c, const void *volt_host, const float *chan_sca
         corr_status s = corr::launch_fengine_range(h, h.fx_volt, chan_scale, h.fx_chan, i0, i1 - i0, st);
         if (s != CORR_OK) return s;
     }
+    CORR_CUDA_TRY(cudaEventRecord(ev[NB + NC + 2], st));
     const bool fused = (h.flags & CORR_FLAG_FUSED_DUMP) != 0;
     const bool store = h.acc_zero;
     const int cb = (h.n_chan + NC - 1) / NC;

@@ -288,3 +288,29 @@ def test_fx_host_pipeline_equals_device_path(cuda_ok, fused):
     c.check_status()
     c.close()
     ref.close()
+
+
+def test_fx_host_back_to_back_calls(cuda_ok):
+    """Calls issued without synchronising in between (the copy-in of one overlaps
+    the previous call's X-engine and copy-out) each return their own cumulative
+    long integration."""
+    n_ant, n_pol, N, K = 16, 2, 64, 128
+    scale = torch.full((N,), 1.0 / 8.0, device=DEV)
+    vs = [synth.volt_int8(n_ant, n_pol, N, K, seed=40 + k) for k in range(3)]
+    ref = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
+    want = []
+    for v in vs:
+        vt = torch.from_numpy(v).to(DEV)
+        ref.xengine(ref.fengine(vt, scale))
+        want.append(ref.dump().cpu().numpy())
+    c = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
+    vh = [torch.from_numpy(v).pin_memory() for v in vs]
+    outs = [torch.zeros((N, c.n_base), dtype=torch.complex128).pin_memory() for _ in vs]
+    for k in range(3):
+        c.fx_host(vh[k], scale, outs[k])
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert np.array_equal(outs[k].numpy(), want[k]), k
+    c.check_status()
+    c.close()
+    ref.close()
