@@ -285,8 +285,11 @@ corr_status corr_get_accum(corr_t *c, void *out, void *stream) {
     Handle &h = c->h;
     if (h.flags & CORR_FLAG_FUSED_DUMP) return CORR_ESTATE;
     corr::DeviceGuard dg(h.device);
-    CORR_CUDA_TRY(cudaMemcpyAsync(out, h.acc, (size_t)h.n_chan * h.n_base * 8, cudaMemcpyDeviceToDevice,
-                                  corr::as_stream(stream)));
+    const size_t bytes = (size_t)h.n_chan * h.n_base * 8;
+    // after a dump (or reset) the accumulator is logically zero; its memory is only
+    // overwritten by the next X-engine launch
+    if (h.acc_zero) CORR_CUDA_TRY(cudaMemsetAsync(out, 0, bytes, corr::as_stream(stream)));
+    else CORR_CUDA_TRY(cudaMemcpyAsync(out, h.acc, bytes, cudaMemcpyDeviceToDevice, corr::as_stream(stream)));
     return CORR_OK;
 }
 

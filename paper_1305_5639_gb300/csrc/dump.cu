@@ -1,23 +1,23 @@
 // Integration dump: the long-integration FP64 buffer receives the integration
-// accumulator (INT32 pairs for INT8, FP32 pairs otherwise), and the accumulator
-// is cleared, in one streaming pass (HBM-bound: read 8 B + read/write 16 B per
-// visibility).
+// accumulator (INT32 pairs for INT8, FP32 pairs otherwise) in one streaming pass
+// (HBM-bound: read 8 B + read/write 16 B per visibility). The accumulator is not
+// rewritten with zeros: the handle marks it clear, so the next X-engine launch
+// overwrites it instead of adding to it and corr_get_accum returns zeros meanwhile.
 #include "internal.h"
 
 namespace corr {
 namespace {
 
 template <typename AccT>
-__global__ void __launch_bounds__(256) k_dump(AccT *__restrict__ acc, double2 *__restrict__ vis, long long n) {
+__global__ void __launch_bounds__(256) k_dump(const AccT *__restrict__ acc, double2 *__restrict__ vis, long long n) {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (; e < n; e += stride) {
-        AccT a = acc[e];
+        const AccT a = __ldcs(acc + e);
         double2 v = vis[e];
         v.x += (double)a.x;
         v.y += (double)a.y;
         vis[e] = v;
-        acc[e] = AccT{0, 0};
     }
 }
 
