@@ -10,8 +10,26 @@ namespace {
 
 template <typename AccT>
 __global__ void __launch_bounds__(256) k_dump(const AccT *__restrict__ acc, double2 *__restrict__ vis, long long n) {
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // four visibilities per thread and round, all loads before any store (more bytes in
+    // flight per thread for the read-modify-write of the FP64 buffer)
+    constexpr int U = 4;
     const long long stride = (long long)gridDim.x * blockDim.x;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e + (U - 1) * stride < n; e += U * stride) {
+        AccT a[U];
+        double2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a[u] = __ldcs(acc + e + u * stride);
+            v[u] = vis[e + u * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u].x += (double)a[u].x;
+            v[u].y += (double)a[u].y;
+            vis[e + u * stride] = v[u];
+        }
+    }
     for (; e < n; e += stride) {
         const AccT a = __ldcs(acc + e);
         double2 v = vis[e];
