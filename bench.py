@@ -572,6 +572,90 @@ def run_calibration(args):
     return 0
 
 
+def run_fp16(args):
+    """FP16 workload: 1024 antennas x 2 pol = 2048 inputs, 2048 spectra per integration,
+    8 integrations dumped to FP64, on a window of --window channels of the 4096 (the
+    per-channel work is identical; the full set would hold 137 GB of complex64 input).
+    One step = 8 integrations (X-engine + dump) of the window. The headline is the hi/lo
+    FP16 X-engine (FP32-class accuracy); plain FP16 and the FP32 CUDA-core X-engine are
+    timed on the same data."""
+    import torch
+
+    from paper_1305_5639_gb300 import build as pbuild
+
+    pbuild.build()
+    from paper_1305_5639_gb300 import api
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n_ant, n_pol, K, n_int = 1024, 2, 2048, 8
+    n_in = n_ant * n_pol
+    W = args.window
+    B = n_in * (n_in + 1) // 2
+    gen = torch.Generator(device=dev).manual_seed(0)
+    X = torch.complex(torch.randn((W, n_in, K), generator=gen, device=dev),
+                      torch.randn((W, n_in, K), generator=gen, device=dev)).contiguous()
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def measure(precision, steps, warmup):
+        # separate dump kernel: measured faster than the dump fused into the FP16 epilogues
+        # (40.0 / 43.4 ms vs 25.6 / 13.5 ms per step for hi/lo / plain), whose FP64 adds
+        # then stall the tensor pipe on GB300's reduced FP64 path
+        c = api.Correlator(n_ant, n_pol, W, K, precision=precision)
+
+        def step():
+            for _ in range(n_int):
+                c.xengine(X)
+                c.dump(copy=False)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        c.check_status()
+        c.close()
+        return a.elapsed_time(b) / steps
+
+    clk = ClockSampler(0)
+    clk.start()
+    hl = measure("fp16_hilo", args.steps, args.warmup)
+    clocks = clk.stop()
+    pl = measure("fp16", args.steps, args.warmup)
+    cc = measure("fp32", 1, 1) if args.comparator else None
+    cm = W * B * K * n_int
+    peaks = _peaks()
+    ach = 8.0 * cm / (hl * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": cm / (hl * 1e-3), "unit": "cMAC/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": hl, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16 hi/lo (f32 accumulate)", "data": "synthetic",
+        "config": {"workload": f"FP16: 1024 antennas x 2 pol = 2048 inputs, 2048 spectra per integration, "
+                               f"8 integrations dumped to FP64, window of {W} of 4096 channels, complex64 N(0,1)",
+                   "l2": f"inputs larger than L2 ({X.numel() * 8 / 1e9:.2f} GB)"},
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_sus"], "unit": "TFLOP/s",
+                     "frac": ach / peaks["bf16_sus"], "traffic": None,
+                     "kernel": "k_to_planar + k_xeng_tma<FP16, 4 planes> + k_dump (hi/lo: 12 MMAs per 16 spectra, "
+                               "3x the algorithmic products)",
+                     "peak_note": f"{peaks['src']} sustained bf16 dense",
+                     "algorithmic": "8 FLOP per complex MAC over packed baselines"},
+        "fp16_plain": {"ms_per_step": pl, "cmac_per_s": cm / (pl * 1e-3),
+                       "tensor_frac": 8.0 * cm / (pl * 1e-3) / 1e12 / peaks["bf16_sus"]},
+        "cudacore_fp32": None if cc is None else {"ms_per_step": cc, "cmac_per_s": cm / (cc * 1e-3),
+                                                 "hilo_speedup": cc / hl},
+        "e2e": None,
+        "gpu_launches": 3 * n_int * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def corr_uses_tc(xengine: str) -> bool:
     return xengine in ("auto", "tcgen05")
 
@@ -582,8 +666,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="B", choices=sorted(WORKLOADS) + ["D", "E"])
-    ap.add_argument("--window", type=int, default=16, help="batched workload: channels per sub-array")
+    ap.add_argument("--workload", default="B", choices=sorted(WORKLOADS) + ["C", "D", "E"])
+    ap.add_argument("--window", type=int, default=16,
+                    help="batched workload: channels per sub-array; FP16 workload: channels of the 4096 (use 32)")
     ap.add_argument("--xengine", default="auto", choices=["auto", "cudacore", "tcgen05"])
     ap.add_argument("--layout", default="planar", choices=["planar", "int8"],
                     help="channelised layout between the engines: planar FP16 codes (TMA X-engine) or complex int8")
@@ -601,6 +686,8 @@ def main():
         return run_batched(args)
     if args.workload == "D":
         return run_calibration(args)
+    if args.workload == "C":
+        return run_fp16(args)
     return run_ours(args)
 
 

@@ -76,11 +76,13 @@ enum { CORR_XENG_AUTO = 0, CORR_XENG_CUDACORE = 1, CORR_XENG_TCGEN05 = 2 };
  *   (CORR_EUNSUPPORTED otherwise); doubles the channelised buffer's size. */
 enum { CORR_FLAG_PLANAR = 1 };
 
-/* CORR_FLAG_FUSED_DUMP (with CORR_FLAG_PLANAR): corr_xengine adds each
- *   integration straight into the FP64 long-integration buffer from its epilogue
- *   (the INT32 sums are exact, so the FP64 sums equal a separate dump's). There is
- *   then no integration accumulator: corr_get_accum returns CORR_ESTATE, and
- *   corr_dump only copies the FP64 buffer out. */
+/* CORR_FLAG_FUSED_DUMP: corr_xengine adds each integration straight into the FP64
+ *   long-integration buffer from its epilogue. Valid with CORR_FLAG_PLANAR (INT8:
+ *   the INT32 sums are exact, so the FP64 sums equal a separate dump's) and with
+ *   CORR_PREC_FP16 / CORR_PREC_FP16_HILO on the AUTO X-engine with n_spectra % 8 == 0
+ *   (the same FP32 tile sums a separate dump would add); CORR_EUNSUPPORTED otherwise.
+ *   There is then no integration accumulator: corr_get_accum returns CORR_ESTATE,
+ *   and corr_dump only copies the FP64 buffer out. */
 enum { CORR_FLAG_FUSED_DUMP = 2 };
 
 typedef struct corr_opts {

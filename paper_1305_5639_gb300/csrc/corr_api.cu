@@ -121,7 +121,11 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
     if (o.precision < CORR_PREC_FP32 || o.precision > CORR_PREC_FP16_HILO) return CORR_EINVAL;
     if (o.xengine < CORR_XENG_AUTO || o.xengine > CORR_XENG_TCGEN05) return CORR_EINVAL;
     if ((o.flags & ~(CORR_FLAG_PLANAR | CORR_FLAG_FUSED_DUMP)) != 0) return CORR_EINVAL;
-    if ((o.flags & CORR_FLAG_FUSED_DUMP) && !(o.flags & CORR_FLAG_PLANAR)) return CORR_EUNSUPPORTED;
+    // the dump fused into the X-engine epilogue exists on the TMA X-engine: INT8 planar,
+    // or FP16 / FP16 hi/lo (AUTO X-engine, n_spectra % 8 == 0)
+    const bool fp16_tma = (o.precision == CORR_PREC_FP16 || o.precision == CORR_PREC_FP16_HILO) &&
+                          o.xengine == CORR_XENG_AUTO && (n_spectra % 8) == 0;
+    if ((o.flags & CORR_FLAG_FUSED_DUMP) && !(o.flags & CORR_FLAG_PLANAR) && !fp16_tma) return CORR_EUNSUPPORTED;
     if ((o.flags & CORR_FLAG_PLANAR) &&
         (o.precision != CORR_PREC_INT8 || o.xengine == CORR_XENG_CUDACORE || (n_spectra % 8) != 0))
         return CORR_EUNSUPPORTED;
@@ -267,8 +271,8 @@ corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, voi
         }
         s = corr::launch_to_planar(h, static_cast<const float2 *>(chan_in), h.planar_ws, npl, st);
         if (s == CORR_OK) s = corr::launch_xengine_tma(h, h.planar_ws, npl, g, store, st);
-    } else if (h.precision == CORR_PREC_FP16_HILO) {
-        s = CORR_EUNSUPPORTED;  // the hi/lo products need the TMA path (n_spectra % 8 == 0)
+    } else if (h.precision == CORR_PREC_FP16_HILO || (h.flags & CORR_FLAG_FUSED_DUMP)) {
+        s = CORR_EUNSUPPORTED;  // the hi/lo products and the fused dump need the TMA path
     } else if (corr::use_tc(h))
         s = corr::launch_xengine_tc(h, chan_in, g, store, st);
     else

@@ -501,31 +501,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                     tc::tmem_ld16(d + 128u + 16u * cb, im);
                     tc::tmem_wait_ld();
                     if (i < itm.n_in) {
+                        const int jb = J0 + 64 * h + 16 * cb;  // columns jb .. jb + 15 of row i
+                        float2 v[16];
 #pragma unroll
                         for (int x = 0; x < 16; ++x) {
-                            const int j = J0 + 64 * h + 16 * cb + x;
-                            if (j <= i) {
-                                float2 v = make_float2(__uint_as_float(re[x]), __uint_as_float(im[x]));
-                                if (p.gains) {
-                                    const float2 gj = __ldg(p.gains + j);
-                                    const float2 w = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
-                                    v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
-                                }
-                                if (p.vis64) {
-                                    double2 *r64 = p.vis64 + (size_t)chan * itm.B + (size_t)i * (i + 1) / 2;
-                                    double2 o = r64[j];
-                                    o.x += (double)v.x;
-                                    o.y += (double)v.y;
-                                    r64[j] = o;
-                                } else {
-                                    if (!p.store) {
-                                        const float2 o = row[j];
-                                        v.x += o.x;
-                                        v.y += o.y;
-                                    }
-                                    row[j] = v;
-                                }
+                            v[x] = make_float2(__uint_as_float(re[x]), __uint_as_float(im[x]));
+                            if (p.gains && jb + x <= i) {
+                                const float2 gj = __ldg(p.gains + jb + x);
+                                const float2 w = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
+                                v[x] = make_float2(v[x].x * w.x - v[x].y * w.y, v[x].x * w.y + v[x].y * w.x);
                             }
+                        }
+                        // read-modify-writes: every read of the row piece in flight before any write
+                        if (p.vis64) {
+                            double2 *r64 = p.vis64 + (size_t)chan * itm.B + (size_t)i * (i + 1) / 2 + jb;
+                            double2 o[16];
+#pragma unroll
+                            for (int x = 0; x < 16; ++x) o[x] = jb + x <= i ? __ldcg(r64 + x) : make_double2(0.0, 0.0);
+#pragma unroll
+                            for (int x = 0; x < 16; ++x)
+                                if (jb + x <= i) r64[x] = make_double2(o[x].x + (double)v[x].x, o[x].y + (double)v[x].y);
+                        } else {
+                            float2 *r = row + jb;
+                            if (!p.store) {
+                                float2 o[16];
+#pragma unroll
+                                for (int x = 0; x < 16; ++x) o[x] = jb + x <= i ? __ldcg(r + x) : make_float2(0.f, 0.f);
+#pragma unroll
+                                for (int x = 0; x < 16; ++x) v[x] = make_float2(v[x].x + o[x].x, v[x].y + o[x].y);
+                            }
+#pragma unroll
+                            for (int x = 0; x < 16; ++x)
+                                if (jb + x <= i) r[x] = v[x];
                         }
                     }
                 }

@@ -241,6 +241,45 @@ def test_tma_fp16_hilo_gains_and_converter_fp16(cuda_ok):
         c.close()
 
 
+@pytest.mark.parametrize("prec", ["fp16", "fp16_hilo"])
+@pytest.mark.parametrize("with_gains", [False, True])
+def test_tma_fp16_fused_dump_equals_separate_dump(cuda_ok, prec, with_gains):
+    """FP16 / hi-lo with the dump fused into the X-engine epilogue: bit-identical to
+    the separate dump (the same FP32 tile sums are added in FP64), three integrations."""
+    from paper_1305_5639_gb300._lib import CorrError, CORR_ESTATE
+
+    n_in, K, n_chan = 200, 136, 3
+    parts = [synth.chan_sources(n_chan, n_in, K, n_src=3, seed=70 + t, src_amp=0.1) for t in range(3)]
+    g = torch.from_numpy(synth.gains(n_in, seed=7)).to(DEV) if with_gains else None
+    sep = api.Correlator(n_in, 1, n_chan, K, precision=prec)
+    fus = api.Correlator(n_in, 1, n_chan, K, precision=prec, fused_dump=True)
+    for X in parts:
+        Xt = torch.from_numpy(X).to(DEV)
+        sep.xengine(Xt, g)
+        sep.dump(copy=False)
+        fus.xengine(Xt, g)
+    a, b = sep.dump().cpu().numpy(), fus.dump().cpu().numpy()
+    fus.check_status()
+    assert np.array_equal(a, b)
+    with pytest.raises(CorrError) as e:
+        fus.accum()
+    assert e.value.status == CORR_ESTATE
+    sep.close()
+    fus.close()
+
+
+def test_fused_dump_flag_validation(cuda_ok):
+    from paper_1305_5639_gb300._lib import CorrError, CORR_EUNSUPPORTED
+
+    for kw in (dict(precision="fp32"), dict(precision="int8"), dict(precision="fp16", xengine="tcgen05")):
+        with pytest.raises(CorrError) as e:
+            api.Correlator(16, 1, 2, 64, fused_dump=True, **kw)
+        assert e.value.status == CORR_EUNSUPPORTED, kw
+    with pytest.raises(CorrError) as e:  # FP16 fused needs n_spectra % 8 == 0
+        api.Correlator(16, 1, 2, 60, precision="fp16", fused_dump=True)
+    assert e.value.status == CORR_EUNSUPPORTED
+
+
 def test_fp16_workload_channel_two_integrations(cuda_ok):
     """The FP16 workload's full channel shape (1024 antennas x 2 pol = 2048 inputs,
     2048 spectra per integration, 3 sources) on one channel, two integrations dumped
