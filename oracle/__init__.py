@@ -23,6 +23,11 @@ What each function follows:
 * ``loss_and_grads`` -- weighted least-squares calibration loss and its analytic
                         gradient (PyTorch convention dL/dRe + j dL/dIm).
 * ``channel_power``  -- per-channel mean power per real component of the spectra.
+* ``channelise_delayed`` -- delay compensation ahead of Eq. 1 (a station-based
+                        function the paper leaves for future work, Section 7):
+                        integer-sample advance of each input's stream, Eq. 1 on the
+                        shifted frames, then a per-channel phase for the fractional
+                        remainder.
 
 Pins (tests/test_oracle.py) tie every function to something outside itself:
 numpy's FFT, closed forms (impulse, constant, delayed source), Parseval, Hermitian
@@ -148,6 +153,38 @@ def channelise(volt: np.ndarray, N: int, bins=None) -> np.ndarray:
         frames = volt.reshape(n_in, K, N)
     S = dft(frames, bins)  # [n_in, K, n_bins]
     return np.ascontiguousarray(np.transpose(S, (2, 0, 1)))
+
+
+# --------------------------------------------------------------------------- delay compensation
+def delay_split(delays: np.ndarray):
+    """tau_i (samples) -> (D_i, f_i): D_i the nearest integer (halves rounded away
+    from zero), f_i = tau_i - D_i in [-0.5, 0.5]. The split is decided on the FP32
+    value, the precision in which delays are handed over."""
+    t = np.asarray(delays, dtype=np.float32).astype(np.float64)
+    D = np.where(t >= 0, np.floor(t + 0.5), -np.floor(-t + 0.5)).astype(np.int64)
+    return D, t - D
+
+
+def channelise_delayed(volt: np.ndarray, N: int, delays: np.ndarray, bins=None) -> np.ndarray:
+    """Delay-compensated channelisation. Input i's stream s_i, delayed by tau_i
+    samples, is advanced by its integer part: s'_i[t] = s_i[t + D_i] (zero where
+    t + D_i falls outside the recorded K*N samples); each N-sample frame goes
+    through Eq. 1; channel k is multiplied by exp(+j 2 pi k f_i / N) for the
+    fractional remainder f_i (k the natural bin index 0..N-1). A delayed tone at a
+    bin frequency comes out with zero phase. Returns [n_bins, n_in, K] complex128."""
+    n_in = volt.shape[0]
+    D, f = delay_split(delays)
+    L = volt.shape[1]
+    shifted = np.zeros_like(volt)
+    for i in range(n_in):
+        d = int(D[i])
+        lo, hi = max(0, -d), min(L, L - d)  # t with 0 <= t + d < L
+        if hi > lo:
+            shifted[i, lo:hi] = volt[i, lo + d:hi + d]
+    S = channelise(shifted, N, bins)
+    k = np.arange(N, dtype=np.float64) if bins is None else np.asarray(bins, dtype=np.float64)
+    ph = np.exp(2j * np.pi * np.outer(k, f) / N)  # [n_bins, n_in]
+    return S * ph[:, :, None]
 
 
 # --------------------------------------------------------------------------- requant

@@ -265,3 +265,59 @@ def test_golden_eq3_triangle_count():
         assert (math.isqrt(8 * nc + 1) - 1) // 2 == ns
         i, j = oracle.tri_pairs(ns)
         assert i.size == nc and np.all(i >= j)
+
+
+# --------------------------------------------------------------------------- delay compensation
+def test_delay_split_rounding():
+    D, f = oracle.delay_split(np.array([0.0, 2.4, 2.5, -2.5, 3.75, -0.2], np.float32))
+    assert D.tolist() == [0, 2, 3, -3, 4, 0]
+    assert np.allclose(f, [0.0, 0.4, -0.5, 0.5, -0.25, -0.2], atol=1e-6)
+
+
+def test_delay_zero_is_plain_channelise():
+    v = synth.volt_fp32(3, 64, 5, seed=2)
+    assert np.array_equal(oracle.channelise_delayed(v, 64, np.zeros(3)), oracle.channelise(v, 64))
+    vi = synth.volt_int8(2, 1, 16, 7, seed=3)
+    assert np.array_equal(oracle.channelise_delayed(vi, 16, np.zeros(2)), oracle.channelise(vi, 16))
+
+
+def test_delay_tone_closed_form():
+    """A tone at bin k0 delayed by tau: exp(j 2 pi k0 (t - tau) / N). Uncompensated,
+    its bin-k0 value is N exp(-j 2 pi k0 tau / N); compensated it is N (zero phase)
+    in every frame whose advanced samples lie inside the record, and the other bins
+    stay empty."""
+    N, K, k0 = 64, 6, 5
+    tau = np.array([0.0, 3.3, -2.7, 70.25], np.float32)
+    t = np.arange(K * N)
+    taud = tau.astype(np.float64)
+    v = np.exp(2j * np.pi * k0 * (t[None, :] - taud[:, None]) / N)
+    S0 = oracle.channelise(v, N)
+    assert np.allclose(S0[k0], N * np.exp(-2j * np.pi * k0 * taud / N)[:, None], atol=1e-9 * N)
+    S = oracle.channelise_delayed(v, N, tau)
+    D, _ = oracle.delay_split(tau)
+    for i in range(len(tau)):
+        a_lo = int(np.ceil(max(0, -D[i]) / N))
+        a_hi = K - int(np.ceil(max(0, D[i]) / N))
+        assert a_hi > a_lo
+        assert np.allclose(S[k0, i, a_lo:a_hi], N, atol=1e-9 * N), i
+        others = np.delete(S[:, i, a_lo:a_hi], k0, axis=0)
+        assert np.max(np.abs(others)) <= 1e-9 * N
+
+
+def test_delay_integer_advance_recovers_source():
+    """Inputs that carry one stream p delayed by whole samples (s_i[t] = p[t - D_i],
+    zero before the stream starts) are re-aligned exactly: every frame whose advanced
+    samples are recorded equals the frame of p, bit for bit."""
+    N, K = 16, 9
+    rng = np.random.default_rng(5)
+    p = rng.standard_normal(K * N) + 1j * rng.standard_normal(K * N)
+    D = np.array([0, 5, 17, 32])
+    v = np.zeros((len(D), K * N), np.complex128)
+    for i, d in enumerate(D):
+        v[i, d:] = p[: K * N - d]
+    S = oracle.channelise_delayed(v, N, D.astype(np.float32))
+    P = oracle.channelise(p[None, :], N)[:, 0, :]
+    for i, d in enumerate(D):
+        a_hi = K - int(np.ceil(d / N))
+        assert np.array_equal(S[:, i, :a_hi], P[:, :a_hi]), i
+        assert np.all(S[:, i, a_hi:] != P[:, a_hi:]) or a_hi == K
