@@ -233,6 +233,11 @@ def run_ours(args):
     corr = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine=args.xengine, planar=planar,
                           fused_dump=fused)
     chan = corr.chan_buffer()
+    if args.delays:
+        # delay compensation: each antenna's integer source delay plus a seeded fractional part
+        dly = np.repeat(synth.delays_int8(n_ant, seed=rank), n_pol).astype(np.float64)
+        dly += np.random.default_rng(rank).uniform(-0.5, 0.5, dly.size)
+        corr.set_delays(dly.astype(np.float32))
     # requantisation scale from a calibration pass: 16 / per-component RMS of each channel
     power = corr.fengine_power(volt)
     scale = (16.0 / torch.sqrt(power)).contiguous()
@@ -378,6 +383,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "int8", "data": "synthetic",
         "config": {"workload": _workload_name(args.workload), "l2": "inputs larger than L2 (4.29 GB per step)",
                    "layout": args.layout, "dump": "fused into the X-engine epilogue" if fused else "separate kernel",
+                   "delay_compensation": bool(args.delays),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "stages_ms": {"fengine": f_ms, "xengine": x_ms, "dump": d_ms},
         "xengine_cmac_per_s": cmac_step / (x_ms * 1e-3),
@@ -673,6 +679,8 @@ def main():
     ap.add_argument("--layout", default="planar", choices=["planar", "int8"],
                     help="channelised layout between the engines: planar FP16 codes (TMA X-engine) or complex int8")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    ap.add_argument("--delays", action="store_true",
+                    help="INT8 workloads: delay compensation in the F-engine (per-input integer + fractional delays)")
     ap.add_argument("--fused-dump", action="store_true",
                     help="planar layout: the X-engine epilogue adds each integration into the FP64 buffer "
                          "directly instead of the separate dump kernel (measured equal on GB300)")

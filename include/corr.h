@@ -129,6 +129,20 @@ CORR_API int64_t corr_n_baselines(const corr_t *h);
 CORR_API corr_status corr_fengine(corr_t *h, const void *volt, const float *chan_scale, void *chan_out,
                          void *stream);
 
+/* Delay compensation fused into the F-engine (a station-based function the paper
+ * leaves for future work, Section 7). delays: host [n_in] float, the delay tau_i
+ * of input i in samples (|tau_i| <= 1e9), or NULL to switch compensation off.
+ * With D_i the nearest integer to tau_i (halves away from zero) and f_i = tau_i - D_i,
+ * corr_fengine and corr_fengine_power then channelise the advanced stream
+ * s'_i[t] = s_i[t + D_i] (zero where t + D_i lies outside the n_spectra * n_chan
+ * recorded samples) and multiply channel k (natural order 0..n_chan-1) by
+ * exp(+j 2 pi k f_i / n_chan); a tone at a bin frequency delayed by tau_i then has
+ * zero phase. The tables live on the device with the handle. Synchronises the
+ * device (kernels already queued may use the previous tables). Returns
+ * CORR_EUNSUPPORTED when n_chan has no F-engine, CORR_EINVAL for a non-finite or
+ * out-of-range delay. */
+CORR_API corr_status corr_set_delays(corr_t *h, const float *delays);
+
 /* Per-channel mean power per real component of the F-engine spectra,
  * power[k] = sum_{i,a} |S_a,i[k]|^2 / (2 n_in n_spectra), in FP32 (atomics; not
  * bit-reproducible). Used to set chan_scale = target_rms / sqrt(power).

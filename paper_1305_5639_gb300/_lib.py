@@ -48,6 +48,7 @@ SIGNATURES = [
     ("corr_n_baselines", ctypes.c_int64, [_P]),
     ("corr_fengine", _S, [_P, _P, _P, _P, _P]),
     ("corr_fengine_power", _S, [_P, _P, _P, _P]),
+    ("corr_set_delays", _S, [_P, _P]),
     ("corr_xengine", _S, [_P, _P, _P, _P]),
     ("corr_get_accum", _S, [_P, _P, _P]),
     ("corr_dump", _S, [_P, _P, _P]),

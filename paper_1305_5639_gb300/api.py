@@ -13,6 +13,8 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
+
 import torch
 
 from . import _lib
@@ -178,6 +180,17 @@ class Correlator:
             out = torch.empty((self.n_chan, self.n_base), dtype=torch.complex128, device=self.device)
         corr_dump(self.h, out if copy else None, stream)
         return out
+
+    def set_delays(self, delays=None):
+        """Per-input delays in samples (sequence of n_in floats) for delay compensation
+        in the F-engine, or None to switch it off."""
+        if delays is None:
+            check(_lib.load().corr_set_delays(self.h, None), "corr_set_delays")
+            return
+        d = np.ascontiguousarray(np.asarray(delays, dtype=np.float32).reshape(-1))
+        if d.size != self.n_in:
+            raise ValueError(f"expected {self.n_in} delays, got {d.size}")
+        check(_lib.load().corr_set_delays(self.h, d.ctypes.data), "corr_set_delays")
 
     def check_status(self, stream=None):
         corr_check_status(self.h, stream)

@@ -51,6 +51,10 @@ void free_buffers(Handle &h) {
     cudaFree(h.acc);
     cudaFree(h.vis64);
     cudaFree(h.twiddle);
+    cudaFree(h.dly_int);
+    cudaFree(h.dly_ph);
+    h.dly_int = nullptr;
+    h.dly_ph = nullptr;
     cudaFree(h.status);
     cudaFree(h.power64);
     cudaFree(h.bwd_ws);
@@ -202,6 +206,54 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
         return CORR_ECUDA;
     }
     *out = c;
+    return CORR_OK;
+}
+
+corr_status corr_set_delays(corr_t *c, const float *delays) {
+    if (!c) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (!corr::fengine_supported(h.n_chan)) return CORR_EUNSUPPORTED;
+    corr::DeviceGuard dg(h.device);
+    // kernels already queued may still read the current tables
+    CORR_CUDA_TRY(cudaDeviceSynchronize());
+    if (!delays) {
+        cudaFree(h.dly_int);
+        cudaFree(h.dly_ph);
+        h.dly_int = nullptr;
+        h.dly_ph = nullptr;
+        return CORR_OK;
+    }
+    const int N = h.n_chan;
+    int T = 1;
+    while (T * T < N) T *= 2;
+    std::vector<int32_t> D((size_t)h.n_in);
+    std::vector<float2> ph((size_t)h.n_in * 2 * T);
+    for (int i = 0; i < h.n_in; ++i) {
+        const double t = (double)delays[i];
+        if (!std::isfinite(t) || std::fabs(t) > 1.0e9) return CORR_EINVAL;
+        // nearest integer, halves away from zero; the remainder f lies in [-0.5, 0.5]
+        const double d = t >= 0 ? std::floor(t + 0.5) : -std::floor(-t + 0.5);
+        const double f = t - d;
+        D[(size_t)i] = (int32_t)d;
+        for (int k = 0; k < T; ++k) {
+            const double a1 = 2.0 * M_PI * (double)k * f / (double)N;
+            const double a2 = 2.0 * M_PI * (double)T * (double)k * f / (double)N;
+            ph[(size_t)i * 2 * T + k] = make_float2((float)std::cos(a1), (float)std::sin(a1));
+            ph[(size_t)i * 2 * T + T + k] = make_float2((float)std::cos(a2), (float)std::sin(a2));
+        }
+    }
+    if (!h.dly_int) {
+        if (cudaMalloc(&h.dly_int, sizeof(int32_t) * (size_t)h.n_in) != cudaSuccess ||
+            cudaMalloc(&h.dly_ph, sizeof(float2) * ph.size()) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h.dly_int);
+            h.dly_int = nullptr;
+            h.dly_ph = nullptr;
+            return CORR_ENOMEM;
+        }
+    }
+    CORR_CUDA_TRY(cudaMemcpy(h.dly_int, D.data(), sizeof(int32_t) * D.size(), cudaMemcpyHostToDevice));
+    CORR_CUDA_TRY(cudaMemcpy(h.dly_ph, ph.data(), sizeof(float2) * ph.size(), cudaMemcpyHostToDevice));
     return CORR_OK;
 }
 

@@ -59,8 +59,9 @@ struct FCfg {
     static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * GS;
     static constexpr size_t pw_bytes = MODE == kPower ? sizeof(float) * N : 0;
     static constexpr size_t tw_bytes = sizeof(float2) * (size_t)N;  // twiddle table copy
+    static constexpr size_t dl_bytes = sizeof(float2) * 32;         // delay phases d[k2] (T <= 32)
     static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW;
-    static constexpr size_t smem = ex_bytes + pw_bytes + tw_bytes + st_bytes;
+    static constexpr size_t smem = ex_bytes + pw_bytes + tw_bytes + dl_bytes + st_bytes;
 };
 
 // 1.5 * 2^23: adding it to |v| <= 2^22 rounds v to the nearest integer (ties to
@@ -101,38 +102,56 @@ __device__ __forceinline__ float2 i8_to_f2(uint32_t w) {
                   make_float2(kMagic + 128.0f, kMagic + 128.0f));
 }
 
-template <int N, bool I8, int MODE>
+template <int N, bool I8, int MODE, bool DLY>
 __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const void *__restrict__ volt,
                                                       const float *__restrict__ scale,
                                                       void *__restrict__ out,
                                                       double *__restrict__ power, int n_in, int K,
-                                                      const float2 *__restrict__ tw_glob, int i0, int vec_out) {
+                                                      const float2 *__restrict__ tw_glob, int i0, int vec_out,
+                                                      const int *__restrict__ dint,
+                                                      const float2 *__restrict__ dph) {
     using C = FCfg<N, I8, MODE>;
     constexpr int T = C::T, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *ex = reinterpret_cast<float *>(smem_raw);                                 // [G][T][EXS]
     float *scs = reinterpret_cast<float *>(smem_raw + C::ex_bytes);                  // [N] (power)
     float2 *tws = reinterpret_cast<float2 *>(smem_raw + C::ex_bytes + C::pw_bytes);  // [k1][t] twiddles
-    uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::ex_bytes + C::pw_bytes + C::tw_bytes);  // staging
+    float2 *dsm = reinterpret_cast<float2 *>(smem_raw + C::ex_bytes + C::pw_bytes + C::tw_bytes);  // [k2] phases
+    uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::ex_bytes + C::pw_bytes + C::tw_bytes +
+                                                 C::dl_bytes);  // staging
     // 16-bit slot of code (k, s) in the swizzled staging rows
     auto slot = [](int k, int s) { return k * (2 * ROWW) + 2 * ((s >> 1) ^ ((k >> 1) & 15)) + (s & 1); };
 
     const int i = i0 + blockIdx.y;
     const int a0 = blockIdx.x * SB;
+    // Delay compensation: the frames are read D samples later in input i's stream
+    // (samples outside the record are zero) and channel k = t + T k2 is multiplied by
+    // c[t] d[k2] = exp(+j 2 pi k f / N): c is folded into the inter-pass twiddles
+    // (it is common to thread t's pass-2 DFT), d applied to the outputs.
+    const long long n_rec = (long long)K * N;  // samples per input
+    const int D = DLY ? __ldg(dint + i) : 0;
     {
         // Warm L2 with this CTA's raw block (SB consecutive spectra of input i, one
         // contiguous range): the loads of the later spectra then hit L2 instead of HBM.
         constexpr int BPS = I8 ? 2 : 8;  // bytes per complex sample
-        const int nvs = min(SB, K - a0);
-        const char *blk = reinterpret_cast<const char *>(volt) + ((size_t)i * K + a0) * N * BPS;
-        const int lines = (nvs * N * BPS + 127) / 128;
-        for (int l = threadIdx.x; l < lines; l += kThreads)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + (size_t)l * 128));
+        const long long lo = max(0LL, (long long)a0 * N + D);
+        const long long hi = min(n_rec, (long long)min(K, a0 + SB) * N + D);
+        if (hi > lo) {
+            const char *blk = reinterpret_cast<const char *>(volt) + ((size_t)i * n_rec + lo) * BPS;
+            const int lines = (int)(((hi - lo) * BPS + 127) / 128);
+            for (int l = threadIdx.x; l < lines; l += kThreads)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + (size_t)l * 128));
+        }
     }
     // per-CTA copy of the twiddle table (shared-memory loads in the FFT loop; measured
     // faster than L1 lookups, while the channel scales are faster from L1)
     for (int m = threadIdx.x; m < N; m += kThreads) {
-        tws[m] = __ldg(tw_glob + m);
+        float2 w = __ldg(tw_glob + m);
+        if constexpr (DLY) {
+            w = cmul(w, __ldg(dph + (size_t)i * 2 * T + m / T));  // table [k1][t]: c[k1]
+            if (m < T) dsm[m] = __ldg(dph + (size_t)i * 2 * T + T + m);
+        }
+        tws[m] = w;
         if constexpr (MODE == kPower) scs[m] = 0.0f;
     }
     __syncthreads();
@@ -153,18 +172,39 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
         const bool valid = (s < SB) && (a < K);
         float2 v[T];
         // ---- pass 1: thread t takes x[t + T m]
-        const size_t base = ((size_t)i * K + (size_t)(valid ? a : 0)) * N + t;
+        // sample offset of this frame in input i's stream (shifted by D with delays)
+        const long long off = (long long)(valid ? a : 0) * N + D;
+        const long long base = (long long)i * n_rec + off + t;
+        // with delays, frames that reach outside the record take the checked loads
+        const bool inside = !DLY || (off >= 0 && off + N <= n_rec);
         if constexpr (I8) {
             const unsigned short *src = reinterpret_cast<const unsigned short *>(volt) + base;
+            if (inside) {
 #pragma unroll
-            for (int m = 0; m < T; ++m) {
-                const uint32_t w = valid ? (uint32_t)__ldg(src + (size_t)T * m) : 0u;
-                v[m] = i8_to_f2(w);
+                for (int m = 0; m < T; ++m) {
+                    const uint32_t w = valid ? (uint32_t)__ldg(src + (size_t)T * m) : 0u;
+                    v[m] = i8_to_f2(w);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < T; ++m) {
+                    const long long n = off + t + T * m;
+                    const uint32_t w = (valid && n >= 0 && n < n_rec) ? (uint32_t)__ldg(src + (long long)T * m) : 0u;
+                    v[m] = i8_to_f2(w);
+                }
             }
         } else {
             const float2 *src = reinterpret_cast<const float2 *>(volt) + base;
+            if (inside) {
 #pragma unroll
-            for (int m = 0; m < T; ++m) v[m] = valid ? __ldg(src + (size_t)T * m) : make_float2(0.f, 0.f);
+                for (int m = 0; m < T; ++m) v[m] = valid ? __ldg(src + (size_t)T * m) : make_float2(0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int m = 0; m < T; ++m) {
+                    const long long n = off + t + T * m;
+                    v[m] = (valid && n >= 0 && n < n_rec) ? __ldg(src + (long long)T * m) : make_float2(0.f, 0.f);
+                }
+            }
         }
         fft_dif<T>(v);  // v[bitrev(k1)] = Y[t][k1]
         sfor<0, T>([&](auto K1) {
@@ -202,6 +242,7 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
                 constexpr int k2 = decltype(K2)::value;
                 const int k = t + T * k2;
                 float2 x = v[bitrev(k2, ilog2(T))];
+                if constexpr (DLY && k2 != 0) x = cmul(x, dsm[k2]);  // delay phase exp(+j 2 pi T k2 f / N)
                 if constexpr (MODE == kRequant || MODE == kRequantPlanar) {
                     const uint32_t q = pack_q<MODE == kRequantPlanar>(x, __ldg(scale + k));
                     reinterpret_cast<uint16_t *>(stg)[slot(k, s)] = (uint16_t)q;
@@ -295,21 +336,31 @@ struct FShape {
     bool i8;
     const float2 *tw;  // [k1][t] table for n_chan = T x T
     int i0 = 0, n_run = -1;  // inputs [i0, i0 + n_run) of the n_in (n_run < 0: all)
+    const int *dint = nullptr;     // per-input integer advance (delay compensation), or null
+    const float2 *dph = nullptr;   // per-input phase tables [n_in][2 T]: c[k1], then d[k2]
 };
 
-template <int N, bool I8, int MODE>
-corr_status launch_one(const FShape &f, const void *volt, const float *scale, void *out, double *power,
+template <int N, bool I8, int MODE, bool DLY>
+corr_status launch_one_(const FShape &f, const void *volt, const float *scale, void *out, double *power,
                        cudaStream_t st) {
     using C = FCfg<N, I8, MODE>;
-    auto kern = k_fengine<N, I8, MODE>;
+    auto kern = k_fengine<N, I8, MODE, DLY>;
     CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
     // 16-byte row stores need 16-byte aligned rows: an aligned buffer and 8 | n_spectra
     const int vec_out = (reinterpret_cast<uintptr_t>(out) % 16 == 0) && (f.n_spectra % 8 == 0);
     // blockIdx.x (the spectra block) varies fastest, so the CTAs resident at one time
     // write neighbouring segments of the same output rows
     dim3 grid((f.n_spectra + C::SB - 1) / C::SB, f.n_run < 0 ? f.n_in : f.n_run);
-    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw, f.i0, vec_out);
+    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw, f.i0, vec_out,
+                                          f.dint, f.dph);
     return check_launch("k_fengine");
+}
+
+template <int N, bool I8, int MODE>
+corr_status launch_one(const FShape &f, const void *volt, const float *scale, void *out, double *power,
+                       cudaStream_t st) {
+    return f.dint ? launch_one_<N, I8, MODE, true>(f, volt, scale, out, power, st)
+                  : launch_one_<N, I8, MODE, false>(f, volt, scale, out, power, st);
 }
 
 template <int MODE>
@@ -330,7 +381,12 @@ corr_status dispatch(const FShape &f, const void *volt, const float *scale, void
 }
 
 FShape shape_of(const Handle &h) {
-    return FShape{h.n_in, h.n_chan, h.n_spectra, h.precision == CORR_PREC_INT8, h.twiddle};
+    FShape f{h.n_in, h.n_chan, h.n_spectra, h.precision == CORR_PREC_INT8, h.twiddle};
+    if (h.dly_int) {
+        f.dint = h.dly_int;
+        f.dph = h.dly_ph;
+    }
+    return f;
 }
 
 __global__ void k_power_finalize(const double *__restrict__ p64, float *__restrict__ out, int n, double inv) {
