@@ -315,6 +315,29 @@ def run_ours(args):
     corr.check_status()
     corr.reset()
 
+    # ---- cross-only rectangle between the two halves of the inputs (space-division block)
+    cross = None
+    if args.cross and planar:
+        h2 = n_in // 2
+        rect = torch.empty((N, h2, n_in - h2, 2), dtype=torch.int32, device=dev)
+        corr.fengine(volt, scale, chan)
+        for _ in range(2):
+            corr.xengine_cross(chan, 0, h2, h2, n_in - h2, out=rect)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(3):
+            corr.xengine_cross(chan, 0, h2, h2, n_in - h2, out=rect)
+        b.record(stream)
+        torch.cuda.synchronize()
+        corr.check_status()
+        r_ms = a.elapsed_time(b) / 3
+        r_cmac = float(N) * h2 * (n_in - h2) * K
+        pk = _peaks()
+        cross = {"inputs": f"[0, {h2}) x [{h2}, {n_in})", "ms": r_ms, "cmac_per_s": r_cmac / (r_ms * 1e-3),
+                 "tensor_frac": 8.0 * r_cmac / (r_ms * 1e-3) / 1e12 / pk["bf16_sus"]}
+        del rect
+
     # ---- CUDA-core comparator at the same accuracy (exact dp4a INT8 X-engine), same data
     cc_ms = None
     if args.comparator:
@@ -393,6 +416,7 @@ def run_ours(args):
         "cudacore_comparator": None if cc_ms is None else {
             "xengine_ms": cc_ms, "cmac_per_s": cmac_step / (cc_ms * 1e-3), "speedup_tensor_vs_cudacore": cc_ms / x_ms,
             "accuracy": "both exact (bit-identical INT32)"},
+        "cross_only_xengine": cross,
         "roofline": roof,
         "roofline_xengine": roof_x,
         "roofline_fengine": roof_f,
@@ -679,6 +703,8 @@ def main():
     ap.add_argument("--layout", default="planar", choices=["planar", "int8"],
                     help="channelised layout between the engines: planar FP16 codes (TMA X-engine) or complex int8")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    ap.add_argument("--cross", action="store_true",
+                    help="INT8 planar workloads: also time the cross-only rectangle between the two input halves")
     ap.add_argument("--delays", action="store_true",
                     help="INT8 workloads: delay compensation in the F-engine (per-input integer + fractional delays)")
     ap.add_argument("--fused-dump", action="store_true",

@@ -183,6 +183,19 @@ CORR_API corr_status corr_fengine_power_noalloc(const void *volt, int32_t n_in, 
  * accumulated since the last dump would exceed the INT32 guard. */
 CORR_API corr_status corr_xengine(corr_t *h, const void *chan_in, const float *gains, void *stream);
 
+/* Cross-only X-engine: the rectangle of the visibility matrix between two input
+ * ranges, V_ij = sum_a X_ai conj(X_aj) for i in [p0, p0 + n_p), j in [q0, q0 + n_q)
+ * (Eq. 2 without the triangle restriction; two disjoint groups give the paper's
+ * space-division node block, Section 3). One integration of chan_in, written to
+ *   vis_out [n_chan][n_p][n_q]: complex int32 (2 x int32) for INT8, complex float
+ *           otherwise; 8-byte aligned device memory, overwritten.
+ * chan_in and gains as for corr_xengine (gains: g_i conj(g_j), float precisions).
+ * The handle's accumulator and long integration are not touched. INT8 needs
+ * CORR_FLAG_PLANAR; FP16 / FP16_HILO the AUTO X-engine with n_spectra % 8 == 0;
+ * otherwise CORR_EUNSUPPORTED. Ranges outside [0, n_in): CORR_EINVAL. */
+CORR_API corr_status corr_xengine_cross(corr_t *h, const void *chan_in, const float *gains, int32_t p0,
+                                        int32_t n_p, int32_t q0, int32_t n_q, void *vis_out, void *stream);
+
 /* Copy the current integration accumulator to out: [n_chan][B] complex int32
  * (2 x int32) for INT8, complex float otherwise. Device pointer. */
 CORR_API corr_status corr_get_accum(corr_t *h, void *out, void *stream);

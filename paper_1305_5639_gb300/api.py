@@ -170,6 +170,18 @@ class Correlator:
         """Whole step from host buffers (pipelined copies); see corr_fx_host."""
         corr_fx_host(self.h, volt_host, chan_scale, vis_host, stream)
 
+    def xengine_cross(self, chan_in, p0: int, n_p: int, q0: int, n_q: int, gains=None, out=None, stream=None):
+        """Cross-only rectangle V_ij, i in [p0, p0 + n_p), j in [q0, q0 + n_q), of one
+        integration: [n_chan, n_p, n_q, 2] int32 (INT8) or [n_chan, n_p, n_q] complex64."""
+        if out is None:
+            if self.precision == "int8":
+                out = torch.empty((self.n_chan, n_p, n_q, 2), dtype=torch.int32, device=self.device)
+            else:
+                out = torch.empty((self.n_chan, n_p, n_q), dtype=torch.complex64, device=self.device)
+        check(_lib.load().corr_xengine_cross(self.h, _ptr(chan_in), _ptr(gains), int(p0), int(n_p), int(q0), int(n_q),
+                                             _ptr(out), _stream(stream)), "corr_xengine_cross")
+        return out
+
     def accum(self, out=None, stream=None):
         out = self.accum_buffer() if out is None else out
         corr_get_accum(self.h, out, stream)

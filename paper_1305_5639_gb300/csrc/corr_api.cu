@@ -336,6 +336,40 @@ corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, voi
     return s;
 }
 
+corr_status corr_xengine_cross(corr_t *c, const void *chan_in, const float *gains, int32_t p0, int32_t n_p,
+                               int32_t q0, int32_t n_q, void *vis_out, void *stream) {
+    if (!c || !chan_in || !vis_out) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (p0 < 0 || q0 < 0 || n_p <= 0 || n_q <= 0 || (int64_t)p0 + n_p > h.n_in || (int64_t)q0 + n_q > h.n_in)
+        return CORR_EINVAL;
+    if (!corr::aligned16(chan_in) || (reinterpret_cast<uintptr_t>(vis_out) & 7u) != 0) return CORR_EINVAL;
+    if (gains && h.precision == CORR_PREC_INT8) return CORR_EINVAL;
+    corr::DeviceGuard dg(h.device);
+    cudaStream_t st = corr::as_stream(stream);
+    const float2 *g = reinterpret_cast<const float2 *>(gains);
+    if (h.precision == CORR_PREC_INT8) {
+        if (!(h.flags & CORR_FLAG_PLANAR)) return CORR_EUNSUPPORTED;
+        return corr::launch_xengine_tma_rect(h, chan_in, 2, nullptr, p0, n_p, q0, n_q, vis_out, st);
+    }
+    const bool fp16 = h.precision == CORR_PREC_FP16 || h.precision == CORR_PREC_FP16_HILO;
+    if (!fp16 || h.xengine != CORR_XENG_AUTO || !corr::xengine_tma_supported(h)) return CORR_EUNSUPPORTED;
+    const int npl = h.precision == CORR_PREC_FP16_HILO ? 4 : 2;
+    const size_t need = (size_t)h.n_chan * npl * h.n_in * h.n_spectra * 2;
+    if (h.planar_ws_bytes < need) {
+        cudaFree(h.planar_ws);
+        h.planar_ws = nullptr;
+        h.planar_ws_bytes = 0;
+        if (cudaMalloc(&h.planar_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return CORR_ENOMEM;
+        }
+        h.planar_ws_bytes = need;
+    }
+    corr_status s = corr::launch_to_planar(h, static_cast<const float2 *>(chan_in), h.planar_ws, npl, st);
+    if (s != CORR_OK) return s;
+    return corr::launch_xengine_tma_rect(h, h.planar_ws, npl, g, p0, n_p, q0, n_q, vis_out, st);
+}
+
 corr_status corr_get_accum(corr_t *c, void *out, void *stream) {
     if (!c || !out) return CORR_EINVAL;
     Handle &h = c->h;

@@ -82,6 +82,10 @@ size_t adj_reduce_scratch_bytes(int n_in);
 inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 corr_status launch_adj_reduce(const float2 *part, double2 *scratch, float2 *dg, int n_in, long long n_part,
                               cudaStream_t st);
+// Cross-only rectangle of the visibility matrix on the TMA X-engine: inputs
+// [p0, p0 + n_p) x [q0, q0 + n_q), output [n_chan][n_p][n_q] overwritten.
+corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl, const float2 *gains, int p0,
+                                    int n_p, int q0, int n_q, void *out, cudaStream_t st);
 bool fengine_supported(int n_chan);
 bool xengine_tma_supported(const Handle &h);
 corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,

@@ -95,6 +95,11 @@ struct TParams {
     float2 *dX;                    // [chan][m][a] or null
     float2 *part;                  // [(chan * nbj + bj) * 2 + half][n_in] or null
     const int *expo;               // [chan - tchan0] power-of-two exponent of A's scaling
+    // cross-only rectangle (rect): rows = inputs p0 .. p0 + n_p - 1, columns = inputs
+    // q0 .. q0 + n_q - 1 of the same planes; rectangular tiles (nbj column blocks);
+    // output [chan][n_p][n_q] (INT32 pairs or float2), overwritten
+    int rect, p0, q0, n_p, n_q;
+    void *rect_out;
 };
 
 // Everything a role needs to know about one work item.
@@ -124,7 +129,7 @@ __device__ __forceinline__ Item get_item(const TParams &p, const CUtensorMap *tm
         r.cpt = sd.cpt;
         r.lg_npad = sd.cpt == 1 ? 7 : (sd.cpt == 2 ? 6 : 5);
         r.n_chan = sd.n_chan;
-    } else if (p.adj) {
+    } else if (p.adj || p.rect) {
         const long long item = blockIdx.x + it * gridDim.x;
         r.chan = (int)(item / p.n_tiles) + p.c0;
         const int t = (int)(item % p.n_tiles);
@@ -217,9 +222,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
             for (long long it = 0; it < my_items; ++it) {
                 const Item itm = get_item(p, &tmap, it);
                 const int chan = itm.chan - p.tchan0, bi = itm.bi, bj = itm.bj;
-                const bool diag = MODE != kAdj && bi == bj;
+                const bool diag = MODE != kAdj && !p.rect && bi == bj;
                 // J side: the same planes as the I side, or conj(X)^T for the adjoint
                 const CUtensorMap *tmj = MODE == kAdj ? &tmapB : itm.tm;
+                // first rows of the I and J blocks (the rectangle's groups start at p0, q0)
+                const int ri = bi * TILE + (p.rect ? p.p0 : 0), rj = bj * TILE + (p.rect ? p.q0 : 0);
                 const int nkb = (itm.K + KB - 1) / KB;
                 bool ok = true;
                 for (int kb = 0; kb < nkb; ++kb, ++n) {
@@ -234,8 +241,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                         tc::mbar_arrive_expect_tx(full_bar(slot), (diag ? NPL : 2 * NPL) * PLANE);
 #pragma unroll
                         for (int pl = 0; pl < NPL; ++pl) {
-                            tc::tma_load_4d(st + (NPL + pl) * PLANE, tmj, s0, bj * TILE, pl, chan, full_bar(slot));
-                            if (!diag) tc::tma_load_4d(st + pl * PLANE, itm.tm, s0, bi * TILE, pl, chan, full_bar(slot));
+                            tc::tma_load_4d(st + (NPL + pl) * PLANE, tmj, s0, rj, pl, chan, full_bar(slot));
+                            if (!diag) tc::tma_load_4d(st + pl * PLANE, itm.tm, s0, ri, pl, chan, full_bar(slot));
                         }
                     } else {
                         // packed small sub-array: cpt channels stacked in one diagonal tile,
@@ -264,7 +271,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
             bool alive = true;
             for (long long it = 0; it < my_items && alive; ++it) {
                 const Item itm = get_item(p, &tmap, it);
-                const bool diag = MODE != kAdj && itm.bi == itm.bj;
+                const bool diag = MODE != kAdj && !p.rect && itm.bi == itm.bj;
                 const int nkb = (itm.K + KB - 1) / KB;
                 const int chunk_kb = MODE == kInt8 ? CHUNK_KB : nkb;
                 uint32_t d_re = 0, d_im = 0;
@@ -416,7 +423,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                             const int q = tr >> itm.lg_npad, qc = tcl >> itm.lg_npad;
                             const int msk = (1 << itm.lg_npad) - 1;
                             const int ii = I0 + (tr & msk), jj = J0 + (tcl & msk);
-                            if (q == qc && chan + q < itm.n_chan && ii < itm.n_in && jj <= ii) {
+                            if (p.rect) {
+                                // rectangle: tile row ii of group P, column jj of group Q
+                                if (ii < p.n_p && jj < p.n_q)
+                                    static_cast<int2 *>(p.rect_out)[((long long)chan * p.n_p + ii) * p.n_q + jj] =
+                                        sl[r * 16 + ((e + r) & 15)];
+                            } else if (q == qc && chan + q < itm.n_chan && ii < itm.n_in && jj <= ii) {
                                 int2 *dst = acc + rbase + (long long)q * itm.B + (long long)ii * (ii + 1) / 2 + jj;
                                 int2 v = sl[r * 16 + ((e + r) & 15)];
                                 if (!p.store) {
@@ -491,23 +503,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                 af_phase[buf] ^= 1u;
                 tc::tc_fence_after();
                 const uint32_t d = tmem + lane_off + (uint32_t)(buf * 256) + (uint32_t)(64 * h);
+                // triangle: row i, columns j <= i of the packed accumulator (or the FP64
+                // buffer); rectangle: row i of group P, columns j < n_q of group Q
+                const bool rowok = p.rect ? i < p.n_p : i < itm.n_in;
+                const int gi0 = p.rect ? p.p0 : 0, gj0 = p.rect ? p.q0 : 0;
                 float2 gi = make_float2(1.f, 0.f);
-                if (p.gains && i < itm.n_in) gi = __ldg(p.gains + i);
-                float2 *row = static_cast<float2 *>(itm.acc) + (size_t)chan * itm.B + (size_t)i * (i + 1) / 2;
+                if (p.gains && rowok) gi = __ldg(p.gains + gi0 + i);
+                float2 *row = p.rect ? static_cast<float2 *>(p.rect_out) + ((size_t)chan * p.n_p + i) * p.n_q
+                                     : static_cast<float2 *>(itm.acc) + (size_t)chan * itm.B + (size_t)i * (i + 1) / 2;
+                const int jend = p.rect ? p.n_q - 1 : i;  // last valid column of this row
 #pragma unroll 1
                 for (int cb = 0; cb < 4; ++cb) {
                     uint32_t re[16], im[16];
                     tc::tmem_ld16(d + 16u * cb, re);
                     tc::tmem_ld16(d + 128u + 16u * cb, im);
                     tc::tmem_wait_ld();
-                    if (i < itm.n_in) {
+                    if (rowok) {
                         const int jb = J0 + 64 * h + 16 * cb;  // columns jb .. jb + 15 of row i
                         float2 v[16];
 #pragma unroll
                         for (int x = 0; x < 16; ++x) {
                             v[x] = make_float2(__uint_as_float(re[x]), __uint_as_float(im[x]));
-                            if (p.gains && jb + x <= i) {
-                                const float2 gj = __ldg(p.gains + jb + x);
+                            if (p.gains && jb + x <= jend) {
+                                const float2 gj = __ldg(p.gains + gj0 + jb + x);
                                 const float2 w = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
                                 v[x] = make_float2(v[x].x * w.x - v[x].y * w.y, v[x].x * w.y + v[x].y * w.x);
                             }
@@ -526,13 +544,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                             if (!p.store) {
                                 float2 o[16];
 #pragma unroll
-                                for (int x = 0; x < 16; ++x) o[x] = jb + x <= i ? __ldcg(r + x) : make_float2(0.f, 0.f);
+                                for (int x = 0; x < 16; ++x) o[x] = jb + x <= jend ? __ldcg(r + x) : make_float2(0.f, 0.f);
 #pragma unroll
                                 for (int x = 0; x < 16; ++x) v[x] = make_float2(v[x].x + o[x].x, v[x].y + o[x].y);
                             }
 #pragma unroll
                             for (int x = 0; x < 16; ++x)
-                                if (jb + x <= i) r[x] = v[x];
+                                if (jb + x <= jend) r[x] = v[x];
                         }
                     }
                 }
@@ -667,6 +685,63 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
         k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
     }
     return check_launch("k_xeng_tma");
+}
+
+corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl, const float2 *gains, int p0,
+                                    int n_p, int q0, int n_q, void *out, cudaStream_t st) {
+    if (n_p <= 0 || n_q <= 0) return CORR_OK;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        set_error_text("cuTensorMapEncodeTiled is not available from the driver");
+        return CORR_EUNSUPPORTED;
+    }
+    if ((h.n_spectra % 8) != 0 || (npl != 2 && npl != 4)) return CORR_EUNSUPPORTED;
+    const int kb = npl == 2 ? 64 : 32;
+    CUtensorMap tmap;
+    const cuuint64_t dims[4] = {(cuuint64_t)h.n_spectra, (cuuint64_t)h.n_in, (cuuint64_t)npl, (cuuint64_t)h.n_chan};
+    const cuuint64_t strides[3] = {(cuuint64_t)h.n_spectra * 2, (cuuint64_t)h.n_spectra * 2 * h.n_in,
+                                   (cuuint64_t)h.n_spectra * 2 * h.n_in * npl};
+    const cuuint32_t box[4] = {(cuuint32_t)kb, TILE, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(planes), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, kb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error_text("cuTensorMapEncodeTiled rejected the planar layout");
+        return CORR_EINVAL;
+    }
+    TParams p{};
+    p.gains = gains;
+    p.status = h.status;
+    p.B = h.n_base;
+    p.rect = 1;
+    p.p0 = p0;
+    p.q0 = q0;
+    p.n_p = n_p;
+    p.n_q = n_q;
+    p.rect_out = out;
+    const int nbi = (n_p + TILE - 1) / TILE;
+    p.nbj = (n_q + TILE - 1) / TILE;
+    p.n_tiles = nbi * p.nbj;
+    p.n_items = (long long)h.n_chan * p.n_tiles;
+    p.n_in = h.n_in;
+    p.K = h.n_spectra;
+    p.store = 1;
+    const unsigned grid = (unsigned)(p.n_items < h.n_sm ? p.n_items : h.n_sm);
+    if (h.precision == CORR_PREC_INT8) {
+        using C = TCfg<2, 64>;
+        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+        k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+    } else if (npl == 2) {
+        using C = TCfg<2, 64>;
+        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+    } else {
+        using C = TCfg<4, 32>;
+        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+    }
+    return check_launch("k_xeng_tma (rectangle)");
 }
 
 // Planar FP16 operand tensor [chan][plane][rows][cols] (cols innermost) with a box
