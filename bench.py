@@ -315,6 +315,29 @@ def run_ours(args):
     corr.check_status()
     corr.reset()
 
+    # ---- short-time visibilities (transient hook): the X-engine with 512-spectrum blocks
+    short_time = None
+    if args.short_time and planar:
+        blk = 512
+        stbuf = corr.set_short_time(blk)
+        corr.fengine(volt, scale, chan)
+        corr.xengine(chan)
+        corr.dump(copy=False)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(3):
+            corr.xengine(chan)
+            corr.dump(copy=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        corr.check_status()
+        corr.set_short_time(out=False)
+        s_ms = a.elapsed_time(b) / 3
+        short_time = {"block_spectra": blk, "xengine_plus_dump_ms": s_ms,
+                      "extra_bytes_per_call": float(stbuf.numel() * 4), "cmac_per_s": cmac_step / (s_ms * 1e-3)}
+        del stbuf
+
     # ---- cross-only rectangle between the two halves of the inputs (space-division block)
     cross = None
     if args.cross and planar:
@@ -417,6 +440,7 @@ def run_ours(args):
             "xengine_ms": cc_ms, "cmac_per_s": cmac_step / (cc_ms * 1e-3), "speedup_tensor_vs_cudacore": cc_ms / x_ms,
             "accuracy": "both exact (bit-identical INT32)"},
         "cross_only_xengine": cross,
+        "short_time_xengine": short_time,
         "roofline": roof,
         "roofline_xengine": roof_x,
         "roofline_fengine": roof_f,
@@ -703,6 +727,8 @@ def main():
     ap.add_argument("--layout", default="planar", choices=["planar", "int8"],
                     help="channelised layout between the engines: planar FP16 codes (TMA X-engine) or complex int8")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    ap.add_argument("--short-time", action="store_true",
+                    help="INT8 planar workloads: also time the X-engine writing 512-spectrum short-time visibilities")
     ap.add_argument("--cross", action="store_true",
                     help="INT8 planar workloads: also time the cross-only rectangle between the two input halves")
     ap.add_argument("--delays", action="store_true",

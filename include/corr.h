@@ -183,6 +183,21 @@ CORR_API corr_status corr_fengine_power_noalloc(const void *volt, int32_t n_in, 
  * accumulated since the last dump would exceed the INT32 guard. */
 CORR_API corr_status corr_xengine(corr_t *h, const void *chan_in, const float *gains, void *stream);
 
+/* Short-time visibilities for a transient detector (a hook between the
+ * cross-multiplication and the accumulation; the paper lists transient detection
+ * as future work, Section 7). With out set, every corr_xengine call (and the
+ * X-engine of corr_fx_host) also writes the visibilities of each block of
+ * block_spectra consecutive spectra, before they are summed into the integration:
+ *   out [n_spectra / block_spectra][n_chan][2][B] int32: per block and channel the
+ *       Re plane then the Im plane of the packed lower triangle; exact integers,
+ *       whose sum over the blocks is that call's integration. Device memory,
+ *       4-byte aligned, owned by the caller, overwritten by each call.
+ * block_spectra: a multiple of 64 in [64, 512] that divides n_spectra. INT8 with
+ * CORR_FLAG_PLANAR only (CORR_EUNSUPPORTED otherwise). out = NULL switches the
+ * output off. The extra bytes written are n_spectra / block_spectra times the
+ * INT32 accumulator's size per call. */
+CORR_API corr_status corr_set_short_time(corr_t *h, int32_t block_spectra, int32_t *out);
+
 /* Cross-only X-engine: the rectangle of the visibility matrix between two input
  * ranges, V_ij = sum_a X_ai conj(X_aj) for i in [p0, p0 + n_p), j in [q0, q0 + n_q)
  * (Eq. 2 without the triangle restriction; two disjoint groups give the paper's

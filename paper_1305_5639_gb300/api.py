@@ -170,6 +170,21 @@ class Correlator:
         """Whole step from host buffers (pipelined copies); see corr_fx_host."""
         corr_fx_host(self.h, volt_host, chan_scale, vis_host, stream)
 
+    def set_short_time(self, block_spectra: int = 512, out=None):
+        """Short-time visibilities of every block of `block_spectra` spectra, written by
+        each X-engine call into `out` ([n_spectra / block, n_chan, 2, B] int32, allocated
+        if None) and returned; set_short_time(out=False) switches the output off."""
+        if out is False:
+            check(_lib.load().corr_set_short_time(self.h, 0, None), "corr_set_short_time")
+            self._st = None
+            return None
+        if out is None:
+            out = torch.zeros((self.n_spectra // block_spectra, self.n_chan, 2, self.n_base), dtype=torch.int32,
+                              device=self.device)
+        check(_lib.load().corr_set_short_time(self.h, int(block_spectra), _ptr(out)), "corr_set_short_time")
+        self._st = out  # keep the buffer alive while the library writes into it
+        return out
+
     def xengine_cross(self, chan_in, p0: int, n_p: int, q0: int, n_q: int, gains=None, out=None, stream=None):
         """Cross-only rectangle V_ij, i in [p0, p0 + n_p), j in [q0, q0 + n_q), of one
         integration: [n_chan, n_p, n_q, 2] int32 (INT8) or [n_chan, n_p, n_q] complex64."""

@@ -257,6 +257,23 @@ corr_status corr_set_delays(corr_t *c, const float *delays) {
     return CORR_OK;
 }
 
+corr_status corr_set_short_time(corr_t *c, int32_t block_spectra, int32_t *out) {
+    if (!c) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (!out) {
+        h.st_out = nullptr;
+        h.st_block = 0;
+        return CORR_OK;
+    }
+    if (h.precision != CORR_PREC_INT8 || !(h.flags & CORR_FLAG_PLANAR)) return CORR_EUNSUPPORTED;
+    if (block_spectra < 64 || block_spectra > 512 || (block_spectra % 64) != 0 || (h.n_spectra % block_spectra) != 0)
+        return CORR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(out) & 3u) != 0) return CORR_EINVAL;
+    h.st_out = out;
+    h.st_block = block_spectra;
+    return CORR_OK;
+}
+
 corr_status corr_destroy(corr_t *c) {
     if (!c) return CORR_OK;
     corr::DeviceGuard dg(c->h.device);

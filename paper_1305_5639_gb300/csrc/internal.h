@@ -23,6 +23,8 @@ struct Handle {
     float2 *twiddle = nullptr;   // F-engine twiddles W_N^(t k1), [k1][t], N = T x T
     int32_t *dly_int = nullptr;  // delay compensation (null: off): integer advance per input
     float2 *dly_ph = nullptr;    //   and phase tables [n_in][2 T]: exp(+j 2 pi k1 f / N), exp(+j 2 pi T k2 f / N)
+    int32_t *st_out = nullptr;   // short-time visibilities (caller's buffer; null: off)
+    int32_t st_block = 0;        //   spectra per block
     int32_t *status = nullptr;   // device status word (0 ok, else CORR_* code set by a kernel)
     double *power64 = nullptr;   // [n_chan] scratch for corr_fengine_power
     void *planar_ws = nullptr;   // FP16 operand planes for the FP16 tensor-core paths (first use)

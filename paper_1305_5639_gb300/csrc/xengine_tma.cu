@@ -100,6 +100,10 @@ struct TParams {
     // output [chan][n_p][n_q] (INT32 pairs or float2), overwritten
     int rect, p0, q0, n_p, n_q;
     void *rect_out;
+    // short-time visibilities (INT8): every block of st_kb stages (64 spectra each) is
+    // also written as [block][chan][plane][B] int32 (plane 0 Re, 1 Im), st_nchan channels
+    int *st_out;
+    int st_kb, st_nchan;
 };
 
 // Everything a role needs to know about one work item.
@@ -168,7 +172,7 @@ __device__ __forceinline__ void decode(long long item, int n_tiles, int &chan, i
     bj = t - r * (r + 1) / 2;
 }
 
-template <int MODE, class C>
+template <int MODE, class C, bool ST = false>
 __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant__ CUtensorMap tmap,
                                                           const __grid_constant__ CUtensorMap tmapB, const TParams p) {
     constexpr int KB = C::KB, NPL = C::NPL, PLANE = C::PLANE, STAGE_BYTES = C::STAGE_BYTES;
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                 const Item itm = get_item(p, &tmap, it);
                 const bool diag = MODE != kAdj && !p.rect && itm.bi == itm.bj;
                 const int nkb = (itm.K + KB - 1) / KB;
-                const int chunk_kb = MODE == kInt8 ? CHUNK_KB : nkb;
+                const int chunk_kb = MODE == kInt8 ? (ST ? p.st_kb : CHUNK_KB) : nkb;
                 uint32_t d_re = 0, d_im = 0;
                 int buf = 0;
                 for (int kb = 0; kb < nkb; ++kb, ++n) {
@@ -343,7 +347,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
             const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
             const int i = I0 + m;
             const int nkb = (itm.K + KB - 1) / KB;
-            const int chunks_per_item = MODE == kInt8 ? (nkb + CHUNK_KB - 1) / CHUNK_KB : 1;
+            const int chunk_kb = ST ? p.st_kb : CHUNK_KB;
+            const int chunks_per_item = MODE == kInt8 ? (nkb + chunk_kb - 1) / chunk_kb : 1;
             if constexpr (MODE == kInt8) {
                 int R[128];  // INT32 sums: Re of j = J0 + 64h + x in R[x], Im in R[64 + x]
 #pragma unroll
@@ -363,8 +368,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                         uint32_t v[16];
                         tc::tmem_ld16(d + (cb < 4 ? 0u : 128u) + 16u * (cb & 3), v);
                         tc::tmem_wait_ld();
+                        // short-time block c of this tile (ST): the 16 columns of the warp's 32
+                        // rows go through the warp's output slice, so that 16 lanes then write
+                        // one row's 64 contiguous bytes
+                        int *sl = reinterpret_cast<int *>(sgen + OFF_OSTG + ew * OSTG_WARP);
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) R[16 * cb + x] += __float2int_rn(__uint_as_float(v[x]));
+                        for (int x = 0; x < 16; ++x) {
+                            const int qx = __float2int_rn(__uint_as_float(v[x]));
+                            R[16 * cb + x] += qx;
+                            if constexpr (ST) sl[lane * 16 + ((x + lane) & 15)] = qx;
+                        }
+                        if constexpr (ST) {
+                            __syncwarp();
+                            const int jb = J0 + 64 * h + 16 * (cb & 3);
+                            int *plane = p.st_out + ((long long)(c * p.st_nchan + chan) * 2 + (cb >> 2)) * itm.B;
+#pragma unroll 1
+                            for (int rr = 0; rr < 16; ++rr) {
+                                const int r = rr * 2 + (lane >> 4), e = lane & 15;
+                                const int ii = I0 + wq * 32 + r, jj = jb + e;
+                                if (ii < itm.n_in && jj <= ii)
+                                    plane[(long long)ii * (ii + 1) / 2 + jj] = sl[r * 16 + ((e + r) & 15)];
+                            }
+                            __syncwarp();
+                        }
                     }
                     tc::tc_fence_before();
                     tc::mbar_arrive(acce_bar(buf));
@@ -670,8 +696,18 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
     p.n_in = h.n_in;
     p.K = h.n_spectra;
     p.store = store ? 1 : 0;
+    if (h.precision == CORR_PREC_INT8 && h.st_out) {
+        p.st_out = h.st_out;
+        p.st_kb = h.st_block / 64;
+        p.st_nchan = h.n_chan;
+    }
     const unsigned grid = (unsigned)(p.n_items < h.n_sm ? p.n_items : h.n_sm);
-    if (h.precision == CORR_PREC_INT8) {
+    if (h.precision == CORR_PREC_INT8 && p.st_out) {
+        using C = TCfg<2, 64>;
+        auto kern = k_xeng_tma<kInt8, C, true>;
+        CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+        kern<<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+    } else if (h.precision == CORR_PREC_INT8) {
         using C = TCfg<2, 64>;
         CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
         k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
