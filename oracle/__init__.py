@@ -23,6 +23,10 @@ What each function follows:
 * ``loss_and_grads`` -- weighted least-squares calibration loss and its analytic
                         gradient (PyTorch convention dL/dRe + j dL/dIm).
 * ``channel_power``  -- per-channel mean power per real component of the spectra.
+* ``channelise_pfb`` -- polyphase filter-bank front end ahead of Eq. 1 (the
+                        windowed multi-tap channeliser the paper's F-engine does
+                        not use, Section 5 / Section 7): each frame is the
+                        tap-weighted sum of n_taps consecutive frames, then Eq. 1.
 * ``channelise_delayed`` -- delay compensation ahead of Eq. 1 (a station-based
                         function the paper leaves for future work, Section 7):
                         integer-sample advance of each input's stream, Eq. 1 on the
@@ -185,6 +189,43 @@ def channelise_delayed(volt: np.ndarray, N: int, delays: np.ndarray, bins=None) 
     k = np.arange(N, dtype=np.float64) if bins is None else np.asarray(bins, dtype=np.float64)
     ph = np.exp(2j * np.pi * np.outer(k, f) / N)  # [n_bins, n_in]
     return S * ph[:, :, None]
+
+
+# --------------------------------------------------------------------------- polyphase filter bank
+def channelise_pfb(volt: np.ndarray, N: int, window: np.ndarray, delays=None, bins=None) -> np.ndarray:
+    """Polyphase filter-bank channelisation. window: [n_taps, N] real weights h[p][n].
+    Spectrum a of input i is Eq. 1 applied to the frame
+        y_a[n] = sum_{p < n_taps} h[p][n] s'_i[(a + p) N + n],   n < N,
+    where s'_i[t] = s_i[t + D_i] is the input's stream advanced by its integer delay
+    (D_i = 0 without `delays`), zero wherever t + D_i is not one of the K*N recorded
+    samples, so every input keeps K spectra; with `delays` channel k is then
+    multiplied by exp(+j 2 pi k f_i / N), as in channelise_delayed.
+    Returns [n_bins, n_in, K] complex128."""
+    h = np.asarray(window, dtype=np.float32).astype(np.float64)
+    P = h.shape[0]
+    assert h.shape == (P, N)
+    n_in = volt.shape[0]
+    if volt.dtype == np.int8:
+        s = volt[..., 0].astype(np.float64) + 1j * volt[..., 1].astype(np.float64)
+    else:
+        s = volt.astype(np.complex128)
+    L = s.shape[1]
+    K = L // N
+    Lp = L + (P - 1) * N  # the frames of the last spectra reach past the record
+    D, f = delay_split(np.zeros(n_in) if delays is None else delays)
+    # s'_i[t] = s_i[t + D_i] for t < Lp, zero where t + D_i is not a recorded sample
+    padded = np.zeros((n_in, Lp), np.complex128)
+    for i in range(n_in):
+        d = int(D[i])
+        lo, hi = max(0, -d), min(Lp, L - d)
+        if hi > lo:
+            padded[i, lo:hi] = s[i, lo + d:hi + d]
+    frames = np.zeros((n_in, K, N), np.complex128)
+    for p in range(P):  # frame a takes frames a .. a + P - 1 of the stream
+        frames += h[p][None, None, :] * padded[:, p * N: p * N + K * N].reshape(n_in, K, N)
+    S = np.ascontiguousarray(np.transpose(dft(frames, bins), (2, 0, 1)))
+    k = np.arange(N, dtype=np.float64) if bins is None else np.asarray(bins, dtype=np.float64)
+    return S * np.exp(2j * np.pi * np.outer(k, f) / N)[:, :, None]
 
 
 # --------------------------------------------------------------------------- requant

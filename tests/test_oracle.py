@@ -321,3 +321,64 @@ def test_delay_integer_advance_recovers_source():
         a_hi = K - int(np.ceil(d / N))
         assert np.array_equal(S[:, i, :a_hi], P[:, :a_hi]), i
         assert np.all(S[:, i, a_hi:] != P[:, a_hi:]) or a_hi == K
+
+
+# --------------------------------------------------------------------------- polyphase filter bank
+def _sinc_hann(P, N):
+    x = (np.arange(P * N) - P * N / 2 + 0.5) / N
+    return (np.sinc(x) * np.hanning(P * N)).reshape(P, N).astype(np.float32)
+
+
+def test_pfb_single_unit_tap_is_channelise():
+    v = synth.volt_fp32(3, 64, 7, seed=4)
+    S = oracle.channelise_pfb(v, 64, np.ones((1, 64), np.float32))
+    assert np.allclose(S, oracle.channelise(v, 64), rtol=0, atol=1e-12 * np.abs(S).max())
+
+
+def test_pfb_single_tap_is_windowed_dft():
+    N, K = 32, 6
+    v = synth.volt_fp32(2, N, K, seed=6)
+    w = np.random.default_rng(1).uniform(0.2, 1.0, N).astype(np.float32)
+    S = oracle.channelise_pfb(v, N, w[None, :])
+    frames = v.reshape(2, K, N).astype(np.complex128) * w.astype(np.float64)[None, None, :]
+    ref = np.transpose(np.fft.fft(frames, axis=-1), (2, 0, 1))
+    assert np.allclose(S, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+def test_pfb_tone_closed_form():
+    """A tone at bin k0: every full frame sum is exp(j 2 pi k0 n / N) H[n] with
+    H[n] = sum_p h[p][n], so S[k] = sum_n H[n] exp(-j 2 pi (k - k0) n / N)."""
+    N, K, P, k0 = 64, 9, 4, 11
+    h = _sinc_hann(P, N)
+    t = np.arange(K * N)
+    v = np.exp(2j * np.pi * k0 * t / N)[None, :]
+    S = oracle.channelise_pfb(v, N, h)[:, 0, :]
+    H = h.astype(np.float64).sum(axis=0)
+    want = np.fft.fft(H)[(np.arange(N) - k0) % N]
+    full = K - P + 1
+    assert np.allclose(S[:, :full], want[:, None], rtol=0, atol=1e-9 * np.abs(want).max())
+
+
+def test_pfb_brute_force_tiny():
+    """Direct double sum over taps and samples, pure Python, on a tiny case with
+    delays (integer advance, zero fill past the record, per-channel phase)."""
+    N, K, P = 8, 5, 3
+    rng = np.random.default_rng(2)
+    v = (rng.standard_normal((2, K * N)) + 1j * rng.standard_normal((2, K * N))).astype(np.complex64)
+    h = rng.uniform(-1, 1, (P, N)).astype(np.float32)
+    tau = np.array([2.25, -9.5], np.float32)
+    S = oracle.channelise_pfb(v, N, h, delays=tau)
+    D, f = oracle.delay_split(tau)
+    for i in range(2):
+        for a in range(K):
+            for k in range(N):
+                acc = 0j
+                for n in range(N):
+                    y = 0j
+                    for p in range(P):
+                        tt = (a + p) * N + n + int(D[i])
+                        if 0 <= tt < K * N:
+                            y += float(h[p, n]) * complex(v[i, tt])
+                    acc += y * np.exp(-2j * np.pi * k * n / N)
+                acc *= np.exp(2j * np.pi * k * f[i] / N)
+                assert abs(S[k, i, a] - acc) <= 1e-9 * (1 + abs(acc))
