@@ -233,6 +233,11 @@ def run_ours(args):
     corr = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine=args.xengine, planar=planar,
                           fused_dump=fused)
     chan = corr.chan_buffer()
+    if args.pfb > 0:
+        # polyphase filter bank: a Hann-windowed sinc of args.pfb taps
+        P = args.pfb
+        x = (np.arange(P * N) - P * N / 2 + 0.5) / N
+        corr.set_pfb((np.sinc(x) * np.hanning(P * N)).reshape(P, N).astype(np.float32))
     if args.delays:
         # delay compensation: each antenna's integer source delay plus a seeded fractional part
         dly = np.repeat(synth.delays_int8(n_ant, seed=rank), n_pol).astype(np.float64)
@@ -430,6 +435,7 @@ def run_ours(args):
         "config": {"workload": _workload_name(args.workload), "l2": "inputs larger than L2 (4.29 GB per step)",
                    "layout": args.layout, "dump": "fused into the X-engine epilogue" if fused else "separate kernel",
                    "delay_compensation": bool(args.delays),
+                   "pfb_taps": args.pfb,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "stages_ms": {"fengine": f_ms, "xengine": x_ms, "dump": d_ms},
         "xengine_cmac_per_s": cmac_step / (x_ms * 1e-3),
@@ -731,6 +737,8 @@ def main():
                     help="INT8 planar workloads: also time the X-engine writing 512-spectrum short-time visibilities")
     ap.add_argument("--cross", action="store_true",
                     help="INT8 planar workloads: also time the cross-only rectangle between the two input halves")
+    ap.add_argument("--pfb", type=int, default=0,
+                    help="INT8 workloads: polyphase filter-bank front end with this many taps (0: plain FFT)")
     ap.add_argument("--delays", action="store_true",
                     help="INT8 workloads: delay compensation in the F-engine (per-input integer + fractional delays)")
     ap.add_argument("--fused-dump", action="store_true",

@@ -143,6 +143,17 @@ CORR_API corr_status corr_fengine(corr_t *h, const void *volt, const float *chan
  * out-of-range delay. */
 CORR_API corr_status corr_set_delays(corr_t *h, const float *delays);
 
+/* Polyphase filter-bank front end for the F-engine (a windowed multi-tap
+ * channeliser; the paper's F-engine is a plain FFT, Section 5). window: host
+ * [n_taps][n_chan] float weights h[p][n] (1 <= n_taps <= 64), or NULL to switch the
+ * filter bank off. corr_fengine and corr_fengine_power then transform, for spectrum
+ * a of input i, the frame y[n] = sum_p h[p][n] s'_i[(a + p) n_chan + n] (s'_i the
+ * stream after any delay compensation, zero past the record, so each input keeps
+ * n_spectra spectra; with delays the per-channel phase follows the transform).
+ * Synchronises the device. CORR_EUNSUPPORTED when n_chan has no F-engine,
+ * CORR_EINVAL for a bad tap count or a non-finite weight. */
+CORR_API corr_status corr_set_pfb(corr_t *h, int32_t n_taps, const float *window);
+
 /* Per-channel mean power per real component of the F-engine spectra,
  * power[k] = sum_{i,a} |S_a,i[k]|^2 / (2 n_in n_spectra), in FP32 (atomics; not
  * bit-reproducible). Used to set chan_scale = target_rms / sqrt(power).

@@ -49,6 +49,7 @@ SIGNATURES = [
     ("corr_fengine", _S, [_P, _P, _P, _P, _P]),
     ("corr_fengine_power", _S, [_P, _P, _P, _P]),
     ("corr_set_delays", _S, [_P, _P]),
+    ("corr_set_pfb", _S, [_P, ctypes.c_int32, _P]),
     ("corr_xengine", _S, [_P, _P, _P, _P]),
     ("corr_set_short_time", _S, [_P, ctypes.c_int32, _P]),
     ("corr_xengine_cross", _S, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]),

@@ -170,6 +170,17 @@ class Correlator:
         """Whole step from host buffers (pipelined copies); see corr_fx_host."""
         corr_fx_host(self.h, volt_host, chan_scale, vis_host, stream)
 
+    def set_pfb(self, window=None):
+        """Polyphase filter-bank window [n_taps, n_chan] (float) for the F-engine, or
+        None to switch the filter bank off."""
+        if window is None:
+            check(_lib.load().corr_set_pfb(self.h, 0, None), "corr_set_pfb")
+            return
+        w = np.ascontiguousarray(np.asarray(window, dtype=np.float32))
+        if w.ndim != 2 or w.shape[1] != self.n_chan:
+            raise ValueError(f"window must be [n_taps, {self.n_chan}]")
+        check(_lib.load().corr_set_pfb(self.h, int(w.shape[0]), w.ctypes.data), "corr_set_pfb")
+
     def set_short_time(self, block_spectra: int = 512, out=None):
         """Short-time visibilities of every block of `block_spectra` spectra, written by
         each X-engine call into `out` ([n_spectra / block, n_chan, 2, B] int32, allocated

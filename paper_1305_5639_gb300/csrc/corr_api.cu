@@ -55,6 +55,10 @@ void free_buffers(Handle &h) {
     cudaFree(h.dly_ph);
     h.dly_int = nullptr;
     h.dly_ph = nullptr;
+    cudaFree(h.pfb_win);
+    cudaFree(h.pfb_y);
+    h.pfb_win = nullptr;
+    h.pfb_y = nullptr;
     cudaFree(h.status);
     cudaFree(h.power64);
     cudaFree(h.bwd_ws);
@@ -254,6 +258,44 @@ corr_status corr_set_delays(corr_t *c, const float *delays) {
     }
     CORR_CUDA_TRY(cudaMemcpy(h.dly_int, D.data(), sizeof(int32_t) * D.size(), cudaMemcpyHostToDevice));
     CORR_CUDA_TRY(cudaMemcpy(h.dly_ph, ph.data(), sizeof(float2) * ph.size(), cudaMemcpyHostToDevice));
+    return CORR_OK;
+}
+
+corr_status corr_set_pfb(corr_t *c, int32_t n_taps, const float *window) {
+    if (!c) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (!corr::fengine_supported(h.n_chan)) return CORR_EUNSUPPORTED;
+    corr::DeviceGuard dg(h.device);
+    // kernels already queued may still read the current window
+    CORR_CUDA_TRY(cudaDeviceSynchronize());
+    if (!window) {
+        cudaFree(h.pfb_win);
+        cudaFree(h.pfb_y);
+        h.pfb_win = nullptr;
+        h.pfb_y = nullptr;
+        h.pfb_taps = 0;
+        return CORR_OK;
+    }
+    if (n_taps < 1 || n_taps > 64) return CORR_EINVAL;
+    const size_t n = (size_t)n_taps * h.n_chan;
+    for (size_t e = 0; e < n; ++e)
+        if (!std::isfinite(window[e])) return CORR_EINVAL;
+    cudaFree(h.pfb_win);
+    h.pfb_win = nullptr;
+    h.pfb_taps = 0;
+    // the FIR output buffer: one complex FP32 frame per (input, spectrum)
+    const size_t y_bytes = sizeof(float2) * (size_t)h.n_in * h.n_spectra * h.n_chan;
+    if (!h.pfb_y && cudaMalloc(&h.pfb_y, y_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        h.pfb_y = nullptr;
+        return CORR_ENOMEM;
+    }
+    if (cudaMalloc(&h.pfb_win, sizeof(float) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return CORR_ENOMEM;
+    }
+    CORR_CUDA_TRY(cudaMemcpy(h.pfb_win, window, sizeof(float) * n, cudaMemcpyHostToDevice));
+    h.pfb_taps = n_taps;
     return CORR_OK;
 }
 

@@ -1,0 +1,413 @@
+// F-engine: per-input channelisation by an unnormalised forward DFT (Eq. 1,
+// Section 2), 8-bit re-packing of the spectra and corner turn to channel-major
+// order, in one pass.
+//
+// Each N = T x T point FFT is computed by T threads in two register passes
+// (four-step / Cooley-Tukey split n = t + T m, k = k1 + T k2):
+//   pass 1: thread t holds x[t + T m], m < T, and computes the T-point DFT over m;
+//           the result is multiplied by W_N^(t k1) (twiddle table, L1-resident)
+//   exchange through shared memory (padded rows, conflict-free)
+//   pass 2: thread k1 holds Y[t][k1], t < T, and computes the T-point DFT over t,
+//           giving X[k1 + T k2].
+// A CTA handles one input and SB consecutive spectra; the outputs are staged in
+// shared memory as [channel][spectrum] so that every (channel, input) row segment
+// of SB spectra is written to global memory contiguously (the corner turn).
+//
+// This header holds the kernel template; the per-feature translation units
+// (fengine_plain.cu, fengine_delay.cu) instantiate it, so that the instantiations
+// compile in parallel, and fengine.cu holds the host entry points.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include <cuda_fp16.h>
+
+#include "fft_common.cuh"
+#include "internal.h"
+
+namespace corr {
+
+// Shape and twiddle table of one F-engine launch.
+struct FShape {
+    int n_in, n_chan, n_spectra;
+    bool i8;
+    const float2 *tw;  // [k1][t] table for n_chan = T x T
+    int i0 = 0, n_run = -1;  // inputs [i0, i0 + n_run) of the n_in (n_run < 0: all)
+    const int *dint = nullptr;     // per-input integer advance (delay compensation), or null
+    const float2 *dph = nullptr;   // per-input phase tables [n_in][2 T]: c[k1], then d[k2]
+};
+
+namespace {
+
+
+constexpr int kThreads = 256;
+
+constexpr int isqrt_pow4(int n) { return n <= 1 ? 1 : 2 * isqrt_pow4(n / 4); }
+
+enum Mode { kFloatOut = 0, kRequant = 1, kPower = 2, kRequantPlanar = 3 };
+
+template <int N, bool I8, int MODE>
+struct FCfg {
+    static constexpr int T = isqrt_pow4(N);
+    static_assert(T * T == N, "N must be a power of 4");
+    static constexpr int G = kThreads / T;  // FFTs in flight per CTA
+    // Exchange buffer of one FFT: T rows of EXS floats; row k1 receives Y[0..T-1][k1]
+    // (one column per writing thread) and is read back as float4. EXS and the per-FFT
+    // stride GS keep both the scalar writes and the float4 reads free of bank conflicts:
+    // 4 EXS / 4 odd per quarter warp, and GS = T (mod 32) so that the FFTs sharing a
+    // warp write to disjoint banks.
+    static constexpr int EXS = T == 4 ? 8 : T + 4;
+    static constexpr int GS = T * EXS + (T == 32 ? 0 : T);
+    static constexpr bool RQ = MODE == kRequant || MODE == kRequantPlanar;
+    // spectra per CTA: the re-packing modes take 32 (64-byte row segments of the
+    // planar FP16 planes, 2 CTAs/SM at N = 1024)
+    static constexpr int SB = MODE == kFloatOut ? 8 : (RQ ? 32 : 16);
+    static_assert(SB % (G < SB ? G : SB) == 0 || G >= SB, "");
+    // staging row stride in 32-bit words. The re-packing modes stage one 16-bit code
+    // pair per (channel k, spectrum s): a row of SB / 2 = 16 words whose word index is
+    // XOR-swizzled with (k >> 1) & 15, so that the 16-bit writes of one warp (32
+    // consecutive rows) and the 4-word row reads of the copy-out are free of bank
+    // conflicts. The FP32 mode stages float2 values in padded rows.
+    static constexpr int ROWW = RQ ? SB / 2 : (MODE == kFloatOut ? 2 * SB + 2 : 0);
+    static_assert(!RQ || ROWW == 16, "swizzle assumes 16-word rows");
+    static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * GS;
+    static constexpr size_t pw_bytes = MODE == kPower ? sizeof(float) * N : 0;
+    static constexpr size_t tw_bytes = sizeof(float2) * (size_t)N;  // twiddle table copy
+    static constexpr size_t dl_bytes = sizeof(float2) * 32;         // delay phases d[k2] (T <= 32)
+    static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW;
+    static constexpr size_t smem = ex_bytes + pw_bytes + tw_bytes + dl_bytes + st_bytes;
+};
+
+// 1.5 * 2^23: adding it to |v| <= 2^22 rounds v to the nearest integer (ties to
+// even, the FP32 adder's rounding) and leaves that integer in the low mantissa bits.
+constexpr float kMagic = 12582912.0f;
+
+// Re-pack to int8: q = clamp(rint(S * scale), -127, 127), round half to even.
+// One FMA adds the magic constant M to the product, which rounds it to an integer
+// kept in the low mantissa bits (rint of the exact product); the clamp is then taken
+// on M + q, which is monotonic in the product for every input, so clamping after
+// rounding equals rounding after clamping. The low byte of each result is the code:
+// two's complement (M = 1.5 * 2^23) or offset binary q + 128 (M + 128, OB).
+template <bool OB>
+__device__ __forceinline__ uint32_t pack_q(float2 v, float sc) {
+    constexpr float M = OB ? kMagic + 128.0f : kMagic;
+    float2 t = f2_fma(v, make_float2(sc, sc), make_float2(M, M));
+    t = make_float2(fminf(fmaxf(t.x, M - 127.0f), M + 127.0f), fminf(fmaxf(t.y, M - 127.0f), M + 127.0f));
+    return __byte_perm(__float_as_uint(t.x), __float_as_uint(t.y), 0x0040);
+}
+
+// Two complex offset-binary codes [re0 im0 re1 im1] (code = q + 128) -> FP16 pairs
+// (q_re0, q_re1) and (q_im0, q_im1), exactly: the half with bits 0x64uu is 1024 + u.
+__device__ __forceinline__ void ob_codes_to_f16_planes(uint32_t u, uint32_t &re, uint32_t &im) {
+    uint32_t hr = __byte_perm(u, 0x64646464u, 0x4240), hi = __byte_perm(u, 0x64646464u, 0x4341);
+    const __half2 k1152 = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480));
+    __half2 r = __hsub2(*reinterpret_cast<__half2 *>(&hr), k1152);
+    __half2 m = __hsub2(*reinterpret_cast<__half2 *>(&hi), k1152);
+    re = *reinterpret_cast<uint32_t *>(&r);
+    im = *reinterpret_cast<uint32_t *>(&m);
+}
+
+// complex int8 sample (16 bits: re in the low byte) -> float2, exactly:
+// (0x4B400000 | (x + 128)) is the float 12582912 + x + 128.
+__device__ __forceinline__ float2 i8_to_f2(uint32_t w) {
+    const uint32_t u = w ^ 0x8080u;
+    return f2_sub(make_float2(__uint_as_float(__byte_perm(u, 0x4B400000u, 0x7650)),
+                              __uint_as_float(__byte_perm(u, 0x4B400000u, 0x7651))),
+                  make_float2(kMagic + 128.0f, kMagic + 128.0f));
+}
+
+// Front-end features of one F-engine instantiation: none, or delay compensation
+// (an integer advance of the frames and / or the per-channel fractional phase).
+enum Feat { kPlain = 0, kDelay = 1 };
+
+template <int N, bool I8, int MODE, int FEAT>
+__global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const void *__restrict__ volt,
+                                                      const float *__restrict__ scale,
+                                                      void *__restrict__ out,
+                                                      double *__restrict__ power, int n_in, int K,
+                                                      const float2 *__restrict__ tw_glob, int i0, int vec_out,
+                                                      const int *__restrict__ dint,
+                                                      const float2 *__restrict__ dph) {
+    using C = FCfg<N, I8, MODE>;
+    constexpr int T = C::T, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
+    constexpr bool DLY = FEAT == kDelay;  // delay code compiled in
+    // the integer advance and the phase are separate: the filter-bank path applies the
+    // advance in its FIR pass and only the phase here
+    const bool has_shift = DLY && dint != nullptr, has_dly = DLY && dph != nullptr;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *ex = reinterpret_cast<float *>(smem_raw);                                 // [G][T][EXS]
+    float *scs = reinterpret_cast<float *>(smem_raw + C::ex_bytes);                  // [N] (power)
+    float2 *tws = reinterpret_cast<float2 *>(smem_raw + C::ex_bytes + C::pw_bytes);  // [k1][t] twiddles
+    float2 *dsm = reinterpret_cast<float2 *>(smem_raw + C::ex_bytes + C::pw_bytes + C::tw_bytes);  // [k2] phases
+    uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::ex_bytes + C::pw_bytes + C::tw_bytes +
+                                                 C::dl_bytes);  // staging
+    // 16-bit slot of code (k, s) in the swizzled staging rows
+    auto slot = [](int k, int s) { return k * (2 * ROWW) + 2 * ((s >> 1) ^ ((k >> 1) & 15)) + (s & 1); };
+
+    const int i = i0 + blockIdx.y;
+    const int a0 = blockIdx.x * SB;
+    // Delay compensation: the frames are read D samples later in input i's stream
+    // (samples outside the record are zero) and channel k = t + T k2 is multiplied by
+    // c[t] d[k2] = exp(+j 2 pi k f / N): c is folded into the inter-pass twiddles
+    // (it is common to thread t's pass-2 DFT), d applied to the outputs.
+    const long long n_rec = (long long)K * N;  // samples per input
+    const int D = has_shift ? __ldg(dint + i) : 0;
+    {
+        // Warm L2 with this CTA's raw block (SB consecutive spectra of input i, one
+        // contiguous range): the loads of the later spectra then hit L2 instead of HBM.
+        constexpr int BPS = I8 ? 2 : 8;  // bytes per complex sample
+        const long long lo = max(0LL, (long long)a0 * N + D);
+        const long long hi = min(n_rec, (long long)min(K, a0 + SB) * N + D);
+        if (hi > lo) {
+            const char *blk = reinterpret_cast<const char *>(volt) + ((size_t)i * n_rec + lo) * BPS;
+            const int lines = (int)(((hi - lo) * BPS + 127) / 128);
+            for (int l = threadIdx.x; l < lines; l += kThreads)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + (size_t)l * 128));
+        }
+    }
+    // per-CTA copy of the twiddle table (shared-memory loads in the FFT loop; measured
+    // faster than L1 lookups, while the channel scales are faster from L1)
+    for (int m = threadIdx.x; m < N; m += kThreads) {
+        float2 w = __ldg(tw_glob + m);
+        if (DLY && has_dly) {
+            w = cmul(w, __ldg(dph + (size_t)i * 2 * T + m / T));  // table [k1][t]: c[k1]
+            if (m < T) dsm[m] = __ldg(dph + (size_t)i * 2 * T + T + m);
+        }
+        tws[m] = w;
+        if constexpr (MODE == kPower) scs[m] = 0.0f;
+    }
+    __syncthreads();
+
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x % T;
+    float *exg = ex + (size_t)g * C::GS;
+    const float4 *exrow = reinterpret_cast<const float4 *>(exg + t * EXS);
+    float pw[T];
+    if constexpr (MODE == kPower) {
+#pragma unroll
+        for (int q = 0; q < T; ++q) pw[q] = 0.0f;
+    }
+
+    for (int s0 = 0; s0 < SB; s0 += G) {
+        const int s = s0 + g;
+        const int a = a0 + s;
+        const bool valid = (s < SB) && (a < K);
+        float2 v[T];
+        // ---- pass 1: thread t takes x[t + T m]
+        // sample offset of this frame in input i's stream (shifted by D with delays)
+        const long long off = (long long)(valid ? a : 0) * N + D;
+        const long long base = (long long)i * n_rec + off + t;
+        // with delays, frames that reach outside the record take the checked loads
+        const bool inside = !DLY || (off >= 0 && off + N <= n_rec);
+        if constexpr (I8) {
+            const unsigned short *src = reinterpret_cast<const unsigned short *>(volt) + base;
+            if (inside) {
+#pragma unroll
+                for (int m = 0; m < T; ++m) {
+                    const uint32_t w = valid ? (uint32_t)__ldg(src + (size_t)T * m) : 0u;
+                    v[m] = i8_to_f2(w);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < T; ++m) {
+                    const long long n = off + t + T * m;
+                    const uint32_t w = (valid && n >= 0 && n < n_rec) ? (uint32_t)__ldg(src + (long long)T * m) : 0u;
+                    v[m] = i8_to_f2(w);
+                }
+            }
+        } else {
+            const float2 *src = reinterpret_cast<const float2 *>(volt) + base;
+            if (inside) {
+#pragma unroll
+                for (int m = 0; m < T; ++m) v[m] = valid ? __ldg(src + (size_t)T * m) : make_float2(0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int m = 0; m < T; ++m) {
+                    const long long n = off + t + T * m;
+                    v[m] = (valid && n >= 0 && n < n_rec) ? __ldg(src + (long long)T * m) : make_float2(0.f, 0.f);
+                }
+            }
+        }
+        fft_dif<T>(v);  // v[bitrev(k1)] = Y[t][k1]
+        sfor<0, T>([&](auto K1) {
+            constexpr int k1 = decltype(K1)::value;
+            // twiddle W_N^(t k1), table laid out [k1][t]
+            if constexpr (k1 != 0) v[bitrev(k1, ilog2(T))] = cmul(v[bitrev(k1, ilog2(T))], tws[k1 * T + t]);
+        });
+        // ---- exchange (Re, then Im; the other half stays in place) and pass 2:
+        // thread t now plays k1 = t and takes Y[tt][k1]
+        sfor<0, T>([&](auto K1) {
+            constexpr int k1 = decltype(K1)::value;
+            exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T))].x;
+        });
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+#pragma unroll
+        for (int j = 0; j < T / 4; ++j) {
+            const float4 r = exrow[j];
+            v[4 * j].x = r.x, v[4 * j + 1].x = r.y, v[4 * j + 2].x = r.z, v[4 * j + 3].x = r.w;
+        }
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+        sfor<0, T>([&](auto K1) {
+            constexpr int k1 = decltype(K1)::value;
+            exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T))].y;
+        });
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+#pragma unroll
+        for (int j = 0; j < T / 4; ++j) {
+            const float4 r = exrow[j];
+            v[4 * j].y = r.x, v[4 * j + 1].y = r.y, v[4 * j + 2].y = r.z, v[4 * j + 3].y = r.w;
+        }
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+        fft_dif<T>(v);  // v[bitrev(k2)] = X[t + T k2]
+        if (valid) {
+            sfor<0, T>([&](auto K2) {
+                constexpr int k2 = decltype(K2)::value;
+                const int k = t + T * k2;
+                float2 x = v[bitrev(k2, ilog2(T))];
+                if constexpr (DLY && k2 != 0) {
+                    if (has_dly) x = cmul(x, dsm[k2]);  // delay phase exp(+j 2 pi T k2 f / N)
+                }
+                if constexpr (MODE == kRequant || MODE == kRequantPlanar) {
+                    const uint32_t q = pack_q<MODE == kRequantPlanar>(x, __ldg(scale + k));
+                    reinterpret_cast<uint16_t *>(stg)[slot(k, s)] = (uint16_t)q;
+                } else if constexpr (MODE == kFloatOut) {
+                    reinterpret_cast<float2 *>(stg)[(size_t)k * (ROWW / 2) + s] = x;
+                } else {
+                    pw[k2] += x.x * x.x + x.y * x.y;
+                }
+            });
+        }
+    }
+
+    if constexpr (MODE != kPower) {
+        __syncthreads();
+        // ---- corner turn: row (k, i) gets spectra a0 .. a0 + nv - 1
+        const int nv = min(SB, K - a0);
+        if constexpr (MODE == kRequantPlanar || MODE == kRequant) {
+            uint16_t *dst = reinterpret_cast<uint16_t *>(out);
+            const uint16_t *sh = reinterpret_cast<const uint16_t *>(stg);
+            // planar FP16 layout [k][plane][i][a]; int8 layout [k][i][a] (complex int8)
+            constexpr int PL = MODE == kRequantPlanar ? 2 : 1;
+            if (nv == SB && vec_out) {
+                // each thread moves 8 spectra of one channel row: 4 staged words
+                // (the code pairs of 2 spectra each) -> one 16-byte store per plane
+                constexpr int CPR = SB / 8;          // 8-spectrum chunks per row
+                constexpr int RPI = kThreads / CPR;  // rows per iteration
+                const int q = threadIdx.x % CPR;
+                int k = threadIdx.x / CPR;
+                // physical words of logical words 4q .. 4q + 3 in row k; the swizzle
+                // (k >> 1) & 15 is the same for k + RPI (RPI / 2 is a multiple of 16)
+                static_assert((RPI / 2) % 16 == 0 || RPI >= N, "");
+                const int h = (k >> 1) & 15;
+                const int o0 = (4 * q) ^ h, o1 = (4 * q + 1) ^ h, o2 = (4 * q + 2) ^ h, o3 = (4 * q + 3) ^ h;
+                const uint32_t *src = stg + (size_t)k * ROWW;
+                uint4 *d = reinterpret_cast<uint4 *>(dst + ((size_t)(PL * k) * n_in + i) * K + a0 + 8 * q);
+                const size_t dstep = (size_t)PL * RPI * n_in * K / 8, dplane = (size_t)n_in * K / 8;
+                for (; k < N; k += RPI, src += RPI * ROWW, d += dstep) {
+                    const uint32_t w0 = src[o0], w1 = src[o1], w2 = src[o2], w3 = src[o3];
+                    if constexpr (MODE == kRequantPlanar) {
+                        uint4 re, im;
+                        ob_codes_to_f16_planes(w0, re.x, im.x);
+                        ob_codes_to_f16_planes(w1, re.y, im.y);
+                        ob_codes_to_f16_planes(w2, re.z, im.z);
+                        ob_codes_to_f16_planes(w3, re.w, im.w);
+                        d[0] = re;
+                        d[dplane] = im;
+                    } else {
+                        d[0] = make_uint4(w0, w1, w2, w3);
+                    }
+                }
+            } else {
+                for (int e = threadIdx.x; e < N * SB; e += kThreads) {
+                    const int k = e / SB, c = e % SB;
+                    if (c < nv) {
+                        const uint16_t code = sh[slot(k, c)];
+                        uint16_t *row0 = dst + ((size_t)(PL * k) * n_in + i) * K + a0;
+                        if constexpr (MODE == kRequantPlanar) {
+                            uint32_t re, im;
+                            ob_codes_to_f16_planes((uint32_t)code, re, im);
+                            row0[c] = (uint16_t)(re & 0xffffu);
+                            row0[(size_t)n_in * K + c] = (uint16_t)(im & 0xffffu);
+                        } else {
+                            row0[c] = code;
+                        }
+                    }
+                }
+            }
+        } else {
+            float2 *dst = reinterpret_cast<float2 *>(out);
+            const float2 *sh = reinterpret_cast<const float2 *>(stg);
+            for (int e = threadIdx.x; e < N * SB; e += kThreads) {
+                int k = e / SB, c = e % SB;
+                if (c < nv) dst[((size_t)k * n_in + i) * K + a0 + c] = sh[(size_t)k * (ROWW / 2) + c];
+            }
+        }
+    }
+
+    if constexpr (MODE == kPower) {
+        sfor<0, T>([&](auto K2) {
+            constexpr int k2 = decltype(K2)::value;
+            atomicAdd(&scs[t + T * k2], pw[k2]);
+        });
+        __syncthreads();
+        for (int m = threadIdx.x; m < N; m += kThreads) atomicAdd(&power[m], (double)scs[m]);
+    }
+}
+
+template <int N, bool I8, int MODE, int FEAT>
+corr_status launch_one_(const FShape &f, const void *volt, const float *scale, void *out, double *power,
+                       cudaStream_t st) {
+    using C = FCfg<N, I8, MODE>;
+    auto kern = k_fengine<N, I8, MODE, FEAT>;
+    CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+    // 16-byte row stores need 16-byte aligned rows: an aligned buffer and 8 | n_spectra
+    const int vec_out = (reinterpret_cast<uintptr_t>(out) % 16 == 0) && (f.n_spectra % 8 == 0);
+    // blockIdx.x (the spectra block) varies fastest, so the CTAs resident at one time
+    // write neighbouring segments of the same output rows
+    dim3 grid((f.n_spectra + C::SB - 1) / C::SB, f.n_run < 0 ? f.n_in : f.n_run);
+    kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw, f.i0, vec_out,
+                                          f.dint, f.dph);
+    return check_launch("k_fengine");
+}
+
+template <int MODE, int FEAT>
+corr_status launch_mode(const FShape &f, const void *volt, const float *scale, void *out, double *power,
+                        cudaStream_t st) {
+#define CORR_F_CASE(NN)                                                                      \
+    case NN:                                                                                 \
+        return f.i8 ? launch_one_<NN, true, MODE, FEAT>(f, volt, scale, out, power, st)      \
+                    : launch_one_<NN, false, MODE, FEAT>(f, volt, scale, out, power, st);
+    switch (f.n_chan) {
+        CORR_F_CASE(16)
+        CORR_F_CASE(64)
+        CORR_F_CASE(256)
+        CORR_F_CASE(1024)
+        default: return CORR_EUNSUPPORTED;
+    }
+#undef CORR_F_CASE
+}
+
+// Every (mode, n_chan, input type) of one front-end feature.
+template <int FEAT>
+corr_status launch_feature(int mode, const FShape &f, const void *volt, const float *scale, void *out,
+                           double *power, cudaStream_t st) {
+    switch (mode) {
+        case kFloatOut: return launch_mode<kFloatOut, FEAT>(f, volt, scale, out, power, st);
+        case kRequant: return launch_mode<kRequant, FEAT>(f, volt, scale, out, power, st);
+        case kPower: return launch_mode<kPower, FEAT>(f, volt, scale, out, power, st);
+        case kRequantPlanar: return launch_mode<kRequantPlanar, FEAT>(f, volt, scale, out, power, st);
+        default: return CORR_EINVAL;
+    }
+}
+
+}  // namespace
+
+// Per-feature entry points, one translation unit each.
+corr_status fengine_run_plain(int mode, const FShape &f, const void *volt, const float *scale, void *out,
+                              double *power, cudaStream_t st);
+corr_status fengine_run_delay(int mode, const FShape &f, const void *volt, const float *scale, void *out,
+                              double *power, cudaStream_t st);
+
+}  // namespace corr

@@ -1,0 +1,11 @@
+// F-engine instantiations with the plain FFT front end (see fengine_kernel.cuh).
+#include "fengine_kernel.cuh"
+
+namespace corr {
+
+corr_status fengine_run_plain(int mode, const FShape &f, const void *volt, const float *scale, void *out,
+                              double *power, cudaStream_t st) {
+    return launch_feature<kPlain>(mode, f, volt, scale, out, power, st);
+}
+
+}  // namespace corr

@@ -23,6 +23,9 @@ struct Handle {
     float2 *twiddle = nullptr;   // F-engine twiddles W_N^(t k1), [k1][t], N = T x T
     int32_t *dly_int = nullptr;  // delay compensation (null: off): integer advance per input
     float2 *dly_ph = nullptr;    //   and phase tables [n_in][2 T]: exp(+j 2 pi k1 f / N), exp(+j 2 pi T k2 f / N)
+    float *pfb_win = nullptr;    // polyphase filter-bank window [pfb_taps][n_chan] (null: off)
+    int32_t pfb_taps = 0;
+    void *pfb_y = nullptr;       //   its FIR output, complex FP32 [n_in][n_spectra][n_chan]
     int32_t *st_out = nullptr;   // short-time visibilities (caller's buffer; null: off)
     int32_t st_block = 0;        //   spectra per block
     int32_t *status = nullptr;   // device status word (0 ok, else CORR_* code set by a kernel)
@@ -88,6 +91,8 @@ corr_status launch_adj_reduce(const float2 *part, double2 *scratch, float2 *dg, 
 // [p0, p0 + n_p) x [q0, q0 + n_q), output [n_chan][n_p][n_q] overwritten.
 corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl, const float2 *gains, int p0,
                                     int n_p, int q0, int n_q, void *out, cudaStream_t st);
+// Polyphase filter bank: FIR pass of inputs [i0, i0 + n_run) into h.pfb_y (pfb.cu).
+corr_status launch_pfb_fir(const Handle &h, const void *volt, int i0, int n_run, cudaStream_t st);
 bool fengine_supported(int n_chan);
 bool xengine_tma_supported(const Handle &h);
 corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
