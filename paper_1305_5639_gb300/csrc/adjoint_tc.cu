@@ -14,12 +14,14 @@
 // channelised data are expected within FP16's normal range, as for the forward
 // FP16 paths.
 //
-// Passes per block of channels:
-//   k_adj_expo   e_f from max |G_f| and max |g|           reads G once
+// Passes:
+//   k_adj_expo   e_f from max |G_f| and max |g|, all channels   reads G once
+// then per block of channels, the operand passes of the next block on a side stream
+// overlapping the GEMM of the current one (two operand buffers):
 //   k_adj_aprep  A_f planes [f][Re_h, Im_h, Re_l, Im_l][m][j]   reads G, writes 8 B / entry
 //   k_adj_bprep  conj(X_f)^T planes [f][4][a][j]           reads X, writes 8 B / sample
 //   k_xeng_tma<kAdj>  GEMM + epilogue (dX, dg partials)
-// then one fixed-order reduction of the dg partials over all channels.
+// and one fixed-order reduction of the dg partials over all channels.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(256) k_adj_bprep(const float2 *__restrict__ X,
 // Workspace layout: [dg partials][reduce scratch][exponents][A planes][B planes],
 // the planes sized for one block of chan_block channels.
 struct TcWs {
-    size_t part, scratch, expo, a, b, total;
+    size_t part, scratch, expo, a[2], b[2], total;
     int cb;
 };
 
@@ -181,19 +183,24 @@ TcWs tc_layout(const Handle &h) {
     TcWs w{};
     const int nbj = (h.n_spectra + 127) / 128;
     const size_t per_chan = 8ull * h.n_in * h.n_in + 8ull * h.n_spectra * h.n_in;  // A + B planes
-    w.cb = (int)std::max<size_t>(1, std::min<size_t>((size_t)h.n_chan, kPlaneBudget / per_chan));
+    const int cb_max = (int)std::max<size_t>(1, std::min<size_t>((size_t)h.n_chan, kPlaneBudget / per_chan));
+    const int n_blk = (h.n_chan + cb_max - 1) / cb_max;
+    w.cb = (h.n_chan + n_blk - 1) / n_blk;  // balanced blocks
     size_t o = 0;
     w.part = o;
     o += align16(sizeof(float2) * (size_t)h.n_chan * nbj * 2 * h.n_in);
     w.scratch = o;
     o += align16(adj_reduce_scratch_bytes(h.n_in));
     w.expo = o;
-    o = (o + sizeof(int) * (size_t)h.n_chan + 1023) & ~(size_t)1023;
-    w.a = o;
-    o += align16(8ull * w.cb * h.n_in * h.n_in);
-    o = (o + 1023) & ~(size_t)1023;
-    w.b = o;
-    o += align16(8ull * w.cb * h.n_spectra * h.n_in);
+    o += sizeof(int) * (size_t)h.n_chan;
+    for (int k = 0; k < 2; ++k) {  // two buffers: block b + 1 is prepared while block b's GEMM runs
+        o = (o + 1023) & ~(size_t)1023;
+        w.a[k] = o;
+        o += align16(8ull * w.cb * h.n_in * h.n_in);
+        o = (o + 1023) & ~(size_t)1023;
+        w.b[k] = o;
+        o += align16(8ull * w.cb * h.n_spectra * h.n_in);
+    }
     w.total = o;
     return w;
 }
@@ -206,28 +213,39 @@ size_t backward_tc_workspace_bytes(const Handle &h, int *chan_block) {
     return w.total;
 }
 
+// The operand passes of block b + 1 run on the side stream `side` while block b's GEMM
+// runs on `st`; ev[0] orders the side stream after `st`'s earlier work, ev[1 + k]
+// marks buffer k prepared, ev[3 + k] buffer k consumed.
 corr_status launch_backward_tc(const Handle &h, const float2 *grad_vis, const float2 *chan_in, const float2 *gains,
-                               float2 *grad_chan, float2 *grad_gains, void *ws, cudaStream_t st) {
+                               float2 *grad_chan, float2 *grad_gains, void *ws, cudaStream_t st,
+                               cudaStream_t side, cudaEvent_t *ev) {
     if ((h.n_in % 8) != 0 || (h.n_spectra % 8) != 0) return CORR_EUNSUPPORTED;
     if (h.n_chan > 65535) return CORR_EUNSUPPORTED;
     const TcWs w = tc_layout(h);
     char *base = static_cast<char *>(ws);
     float2 *part = grad_gains ? reinterpret_cast<float2 *>(base + w.part) : nullptr;
     int *expo = reinterpret_cast<int *>(base + w.expo);
-    __half *A = reinterpret_cast<__half *>(base + w.a);
-    __half *Bt = reinterpret_cast<__half *>(base + w.b);
     const int nt_in = (h.n_in + kTile - 1) / kTile, nt_k = (h.n_spectra + kTile - 1) / kTile;
-    for (int c0 = 0; c0 < h.n_chan; c0 += w.cb) {
-        const int c1 = std::min(h.n_chan, c0 + w.cb), nc = c1 - c0;
-        k_adj_expo<<<nc, 256, 0, st>>>(grad_vis, gains, expo + c0, h.n_in, h.n_base, c0);
-        corr_status s = check_launch("k_adj_expo");
-        if (s != CORR_OK) return s;
-        k_adj_aprep<<<dim3(nt_in, nt_in, nc), 256, 0, st>>>(grad_vis, gains, expo + c0, A, h.n_in, h.n_base, c0);
+    CORR_CUDA_TRY(cudaEventRecord(ev[0], st));
+    CORR_CUDA_TRY(cudaStreamWaitEvent(side, ev[0], 0));
+    k_adj_expo<<<h.n_chan, 256, 0, side>>>(grad_vis, gains, expo, h.n_in, h.n_base, 0);
+    corr_status s = check_launch("k_adj_expo");
+    if (s != CORR_OK) return s;
+    int blk = 0;
+    for (int c0 = 0; c0 < h.n_chan; c0 += w.cb, ++blk) {
+        const int c1 = std::min(h.n_chan, c0 + w.cb), nc = c1 - c0, k = blk & 1;
+        __half *A = reinterpret_cast<__half *>(base + w.a[k]);
+        __half *Bt = reinterpret_cast<__half *>(base + w.b[k]);
+        if (blk >= 2) CORR_CUDA_TRY(cudaStreamWaitEvent(side, ev[3 + k], 0));  // GEMM of block - 2 done
+        k_adj_aprep<<<dim3(nt_in, nt_in, nc), 256, 0, side>>>(grad_vis, gains, expo + c0, A, h.n_in, h.n_base, c0);
         if ((s = check_launch("k_adj_aprep")) != CORR_OK) return s;
-        k_adj_bprep<<<dim3(nt_k, nt_in, nc), 256, 0, st>>>(chan_in, Bt, h.n_in, h.n_spectra, c0);
+        k_adj_bprep<<<dim3(nt_k, nt_in, nc), 256, 0, side>>>(chan_in, Bt, h.n_in, h.n_spectra, c0);
         if ((s = check_launch("k_adj_bprep")) != CORR_OK) return s;
+        CORR_CUDA_TRY(cudaEventRecord(ev[1 + k], side));
+        CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + k], 0));
         s = launch_adjoint_tma(h, A, Bt, expo + c0, chan_in, gains, grad_chan, part, c0, c1, st);
         if (s != CORR_OK) return s;
+        CORR_CUDA_TRY(cudaEventRecord(ev[3 + k], st));
     }
     if (!grad_gains) return CORR_OK;
     const int nbj = (h.n_spectra + 127) / 128;

@@ -74,6 +74,12 @@ void free_buffers(Handle &h) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
     }
+    if (h.bwd_side) cudaStreamDestroy(h.bwd_side);
+    h.bwd_side = nullptr;
+    for (cudaEvent_t &e : h.bwd_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
     h.acc = nullptr;
     h.vis64 = nullptr;
     h.twiddle = nullptr;
@@ -576,10 +582,19 @@ corr_status corr_backward(corr_t *c, const float *grad_vis, const void *chan_in,
             }
             h.bwd_ws_bytes = need;
         }
+        if (!h.bwd_side) {
+            bool ok = cudaStreamCreateWithFlags(&h.bwd_side, cudaStreamNonBlocking) == cudaSuccess;
+            for (cudaEvent_t &e : h.bwd_ev)
+                ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                return CORR_ECUDA;
+            }
+        }
         return corr::launch_backward_tc(h, reinterpret_cast<const float2 *>(grad_vis),
                                         static_cast<const float2 *>(chan_in), reinterpret_cast<const float2 *>(gains),
                                         reinterpret_cast<float2 *>(grad_chan), reinterpret_cast<float2 *>(grad_gains),
-                                        h.bwd_ws, corr::as_stream(stream));
+                                        h.bwd_ws, corr::as_stream(stream), h.bwd_side, h.bwd_ev);
     }
     if (grad_gains) {
         const size_t need = corr::backward_workspace_bytes(h);

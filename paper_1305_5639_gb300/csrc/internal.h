@@ -33,6 +33,8 @@ struct Handle {
     void *planar_ws = nullptr;   // FP16 operand planes for the FP16 tensor-core paths (first use)
     size_t planar_ws_bytes = 0;
     float2 *bwd_ws = nullptr;    // corr_backward workspace (dg partials; tensor-core operand planes)
+    cudaStream_t bwd_side = nullptr;  // tensor-core backward: side stream for the operand passes
+    cudaEvent_t bwd_ev[5] = {};       //   and its events
     // host-buffer pipeline (corr_fx_host): device copies of the inputs and the
     // channelised data, two copy streams and per-block events (first use)
     void *fx_volt = nullptr, *fx_chan = nullptr;
@@ -77,7 +79,8 @@ corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const fl
 // whole backward pass, and its dX GEMM (see adjoint_tc.cu, xengine_tma.cu).
 size_t backward_tc_workspace_bytes(const Handle &h, int *chan_block);
 corr_status launch_backward_tc(const Handle &h, const float2 *grad_vis, const float2 *chan_in, const float2 *gains,
-                               float2 *grad_chan, float2 *grad_gains, void *ws, cudaStream_t st);
+                               float2 *grad_chan, float2 *grad_gains, void *ws, cudaStream_t st,
+                               cudaStream_t side, cudaEvent_t *ev);
 corr_status launch_adjoint_tma(const Handle &h, const void *a_planes, const void *b_planes, const int *expo,
                                const float2 *X, const float2 *gains, float2 *dX, float2 *part, int c0, int c1,
                                cudaStream_t st);
