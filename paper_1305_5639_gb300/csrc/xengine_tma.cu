@@ -43,8 +43,10 @@ namespace {
 
 constexpr int TILE = 128;
 constexpr int NSTAGE = 3;
+constexpr bool kInt8Wide = true;  // INT8 triangle launches use the wide (N = 256) MMA form
 constexpr int NEPI = 256;                 // epilogue threads (warps 4..11)
 constexpr int NTHREADS = 384;
+constexpr int NTHREADS_WIDE = 640;        // wide INT8 form: 16 epilogue warps (warps 4..19)
 constexpr int OSTG_WARP = 4096;           // per epilogue warp: a 32-row slice of the output tile
 
 // Stage geometry. NPL planes per operand side (2: Re, Im; 4: Re_h, Im_h, Re_l, Im_l
@@ -172,11 +174,19 @@ __device__ __forceinline__ void decode(long long item, int n_tiles, int &chan, i
     bj = t - r * (r + 1) / 2;
 }
 
-template <int MODE, class C, bool ST = false>
-__global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant__ CUtensorMap tmap,
+template <int MODE, class C, bool ST = false, bool WIDE = false>
+__global__ void __launch_bounds__(WIDE ? NTHREADS_WIDE : NTHREADS, 1) k_xeng_tma(const __grid_constant__ CUtensorMap tmap,
                                                           const __grid_constant__ CUtensorMap tmapB, const TParams p) {
     constexpr int KB = C::KB, NPL = C::NPL, PLANE = C::PLANE, STAGE_BYTES = C::STAGE_BYTES;
     constexpr int CHUNK_KB = C::CHUNK_KB, OFF_OSTG = C::OFF_OSTG, OFF_BAR = C::OFF_BAR;
+    // wide INT8 form: per 16 spectra two N = 256 MMAs, D1 += Re_I [Re_J; Im_J]^T and
+    // D2 += Im_I [Re_J; Im_J]^T (the J stage's two planes form one 256-row operand), so
+    // each operand tile is read from shared memory once per MMA pair instead of twice;
+    // the epilogue forms Re V = D1a + D2b and Im V = D2a - D1b in INT32. Each half of D1,
+    // D2 sums one kind of product, |.| <= 127^2 per spectrum, so 1024-spectrum FP32 chunks
+    // stay exact; D1 and D2 fill TMEM, so the accumulator is single-buffered.
+    constexpr bool W = WIDE && MODE == kInt8 && NPL == 2 && !ST;
+    constexpr int CHUNK = MODE == kInt8 ? (W ? 2 * CHUNK_KB : CHUNK_KB) : 0;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -199,7 +209,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(accf_bar(b), 1);
-            tc::mbar_init(acce_bar(b), NEPI);
+            tc::mbar_init(acce_bar(b), W ? 2 * NEPI : NEPI);
         }
         tc::mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -270,6 +280,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
         if (lane == 0) {
             constexpr uint32_t ID = tc::idesc_f16(128, 128);
             constexpr uint32_t ID_NEG = tc::idesc_f16(128, 128, /*neg_a=*/true);
+            constexpr uint32_t ID256 = tc::idesc_f16(128, 256);
             uint32_t ae_phase[2] = {0, 0};
             long long n = 0, ch = 0;  // stage and accumulator-chunk counters
             bool alive = true;
@@ -277,13 +288,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                 const Item itm = get_item(p, &tmap, it);
                 const bool diag = MODE != kAdj && !p.rect && itm.bi == itm.bj;
                 const int nkb = (itm.K + KB - 1) / KB;
-                const int chunk_kb = MODE == kInt8 ? (ST ? p.st_kb : CHUNK_KB) : nkb;
-                uint32_t d_re = 0, d_im = 0;
+                const int chunk_kb = MODE == kInt8 ? (ST ? p.st_kb : CHUNK) : nkb;
+                uint32_t d_re = 0, d_im = 0;  // wide form: D1 and D2
                 int buf = 0;
                 for (int kb = 0; kb < nkb; ++kb, ++n) {
                     const int kin = kb % chunk_kb;
                     if (kin == 0) {
-                        buf = (int)(ch & 1);
+                        buf = W ? 0 : (int)(ch & 1);
                         if (!tc::mbar_wait(acce_bar(buf), ae_phase[buf] ^ 1u, abort_flag, p.status)) {
                             alive = false;
                             break;
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
                         ae_phase[buf] ^= 1u;
                         tc::tc_fence_after();
                         d_re = tmem + (uint32_t)(buf * 256);
-                        d_im = d_re + 128u;
+                        d_im = d_re + (W ? 256u : 128u);
                     }
                     const int slot = (int)(n % NSTAGE);
                     if (!tc::mbar_wait(full_bar(slot), (uint32_t)((n / NSTAGE) & 1), abort_flag, p.status)) {
@@ -314,10 +325,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
 #pragma unroll
                     for (int k = 0; k < KB / 16; ++k) {
                         const uint32_t ko = 32u * k;
-                        cmma(a0, b0, ko, (kin > 0 || k > 0) ? 1u : 0u);  // h h
-                        if constexpr (NPL == 4) {
-                            cmma(a0, b0 + 2 * PLANE, ko, 1u);           // h l
-                            cmma(a0 + 2 * PLANE, b0, ko, 1u);           // l h
+                        if constexpr (W) {
+                            const uint32_t acc = (kin > 0 || k > 0) ? 1u : 0u;
+                            const uint64_t bb = C::desc(b0 + ko);  // [Re_J; Im_J], 256 rows
+                            tc::mma_f16(d_re, C::desc(a0 + ko), bb, ID256, acc);
+                            tc::mma_f16(d_im, C::desc(a0 + PLANE + ko), bb, ID256, acc);
+                        } else {
+                            cmma(a0, b0, ko, (kin > 0 || k > 0) ? 1u : 0u);  // h h
+                            if constexpr (NPL == 4) {
+                                cmma(a0, b0 + 2 * PLANE, ko, 1u);           // h l
+                                cmma(a0 + 2 * PLANE, b0, ko, 1u);           // l h
+                            }
                         }
                     }
                     tc::mma_commit(empty_bar(slot));
@@ -331,6 +349,82 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
             tc::mbar_wait(drain_bar, 0u, abort_flag, p.status, 1000000000ull, false);
         }
         __syncwarp();
+    } else if (W && warp >= 4) {
+        // ------------------------------------------------------------ wide INT8 epilogue
+        // 16 warps, four per TMEM lane quarter, each owning 32 columns of Re V and Im V:
+        // the single-buffered accumulator is drained twice as fast as by 8 warps
+        const int ew = warp - 4;               // 0..15
+        const int wq = warp & 3;               // TMEM lane quarter this warp may access
+        const int qc = ew >> 2;                // column quarter: j in [32 qc, 32 qc + 32)
+        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+        uint32_t af_phase = 0;
+        bool alive = true;
+        for (long long it = 0; it < my_items && alive; ++it) {
+            const Item itm = get_item(p, &tmap, it);
+            const int chan = itm.chan;
+            const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
+            const int nkb = (itm.K + KB - 1) / KB;
+            const int chunks = (nkb + CHUNK - 1) / CHUNK;
+            int R[64];  // INT32 sums: Re of j = J0 + 32 qc + x in R[x], Im in R[32 + x]
+#pragma unroll
+            for (int x = 0; x < 64; ++x) R[x] = 0;
+            for (int c = 0; c < chunks; ++c) {
+                if (!tc::mbar_wait(accf_bar(0), af_phase, abort_flag, p.status)) {
+                    alive = false;
+                    break;
+                }
+                af_phase ^= 1u;
+                tc::tc_fence_after();
+                const uint32_t d = tmem + lane_off + (uint32_t)(32 * qc);
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    // D1 = (ar br | ar bi) in columns 0..255, D2 = (ai br | ai bi) in 256..511
+                    uint32_t u[8], w[8];
+                    tc::tmem_ld8(d + 8u * cb, u);         // ar br
+                    tc::tmem_ld8(d + 384u + 8u * cb, w);  // ai bi
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int x = 0; x < 8; ++x)
+                        R[8 * cb + x] += __float2int_rn(__uint_as_float(u[x])) + __float2int_rn(__uint_as_float(w[x]));
+                    tc::tmem_ld8(d + 256u + 8u * cb, u);  // ai br
+                    tc::tmem_ld8(d + 128u + 8u * cb, w);  // ar bi
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int x = 0; x < 8; ++x)
+                        R[32 + 8 * cb + x] += __float2int_rn(__uint_as_float(u[x])) - __float2int_rn(__uint_as_float(w[x]));
+                }
+                tc::tc_fence_before();
+                tc::mbar_arrive(acce_bar(0));
+            }
+            if (!alive) break;
+            // write the tile's INT32 sums through the warp's 2 KB shared-memory slice,
+            // 8 columns at a time, so that 8 lanes write one row's 64 contiguous bytes
+            int2 *sl = reinterpret_cast<int2 *>(sgen + OFF_OSTG + ew * (OSTG_WARP / 2));
+            int2 *acc = static_cast<int2 *>(itm.acc);
+            const long long rbase = (long long)chan * itm.B;
+#pragma unroll
+            for (int sc = 0; sc < 4; ++sc) {
+#pragma unroll
+                for (int x = 0; x < 8; ++x) sl[lane * 8 + ((x + lane) & 7)] = make_int2(R[8 * sc + x], R[32 + 8 * sc + x]);
+                __syncwarp();
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) {
+                    const int r = rr * 4 + (lane >> 3), e = lane & 7;
+                    const int ii = I0 + wq * 32 + r, jj = J0 + 32 * qc + 8 * sc + e;
+                    if (ii < itm.n_in && jj <= ii) {
+                        int2 *dst = acc + rbase + (long long)ii * (ii + 1) / 2 + jj;
+                        int2 v = sl[r * 8 + ((e + r) & 7)];
+                        if (!p.store) {
+                            const int2 o = *dst;
+                            v.x += o.x;
+                            v.y += o.y;
+                        }
+                        *dst = v;
+                    }
+                }
+                __syncwarp();
+            }
+        }
     } else if (warp >= 4) {
         // ------------------------------------------------------------ epilogue
         const int ew = warp - 4;               // 0..7
@@ -347,7 +441,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_xeng_tma(const __grid_constant_
             const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
             const int i = I0 + m;
             const int nkb = (itm.K + KB - 1) / KB;
-            const int chunk_kb = ST ? p.st_kb : CHUNK_KB;
+            const int chunk_kb = ST ? p.st_kb : CHUNK;
             const int chunks_per_item = MODE == kInt8 ? (nkb + chunk_kb - 1) / chunk_kb : 1;
             if constexpr (MODE == kInt8) {
                 int R[128];  // INT32 sums: Re of j = J0 + 64h + x in R[x], Im in R[64 + x]
@@ -709,8 +803,14 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
         kern<<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
     } else if (h.precision == CORR_PREC_INT8) {
         using C = TCfg<2, 64>;
-        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+        if (kInt8Wide && !p.vis64) {
+            auto kern = k_xeng_tma<kInt8, C, false, true>;
+            CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+            kern<<<grid, NTHREADS_WIDE, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+        } else {
+            CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+            k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+        }
     } else if (npl == 2) {
         using C = TCfg<2, 64>;
         CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
