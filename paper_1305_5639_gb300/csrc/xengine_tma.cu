@@ -16,11 +16,20 @@
 // 512 spectra, the epilogue converts the other exactly and adds it into INT32
 // running sums held in registers. The result is bit-exact.
 //
-// Warp roles (384 threads, one persistent CTA per SM):
+// INT8 triangle launches use the wide form instead (the kernel's WIDE variant):
+// two N = 256 MMAs per 16 spectra, D1 += re_I [re_J; im_J]^T and
+// D2 += im_I [re_J; im_J]^T, with Re V = D1a + D2b and Im V = D2a - D1b formed in
+// INT32 by the epilogue; it reads 25% fewer operand bytes from shared memory per
+// product (the narrow form's limit), folds every 1024 spectra (each half of D1, D2
+// sums one kind of product) and, D1 and D2 filling TMEM, single-buffers the
+// accumulator.
+//
+// Warp roles (one persistent CTA per SM; 384 threads, 640 in the wide form):
 //   warp 0       TMA producer (one thread): 3-stage ring of 64-spectrum stages
 //   warp 1       TMEM allocator + single-thread MMA issuer
 //   warps 4-11   epilogue, two warps per TMEM lane quarter, each owning half of
-//                the tile's columns and their INT32 sums
+//                the tile's columns and their INT32 sums (wide form: warps 4-19,
+//                four per lane quarter, a quarter of the columns each)
 // Every mbarrier wait is bounded; on time-out the CTA records CORR_ETIMEOUT and
 // every role leaves its loop.
 //
