@@ -109,14 +109,37 @@ __device__ __forceinline__ void ob_codes_to_f16_planes(uint32_t u, uint32_t &re,
     im = *reinterpret_cast<uint32_t *>(&m);
 }
 
-// complex int8 sample (16 bits: re in the low byte) -> float2, exactly:
-// (0x4B400000 | (x + 128)) is the float 12582912 + x + 128.
-__device__ __forceinline__ float2 i8_to_f2(uint32_t w) {
+// complex int8 sample x (16 bits: re in the low byte) -> float2 (c + 256 re, c + 256 im)
+// with the constant c = 2^23 + 2^15, exactly: the float with bits 0x4B00 (x + 128) 00
+// is 2^23 + 256 (x + 128). The offset needs no subtraction here: the first radix-2
+// stage's differences cancel it exactly, and along the all-sums path (DFT bin 0 of
+// pass 1) every partial sum j c + 256 s stays exact (a multiple of 256 below 2^29,
+// where the spacing of floats is at most 32), so that bin is corrected once per FFT
+// (kOffsetFix). The factor 256 leaves every rounding unchanged (a power of two); it
+// is divided out by the inter-pass twiddles, stored divided by 256.
+__device__ __forceinline__ float2 i8_to_f2_scaled(uint32_t w) {
     const uint32_t u = w ^ 0x8080u;
-    return f2_sub(make_float2(__uint_as_float(__byte_perm(u, 0x4B400000u, 0x7650)),
-                              __uint_as_float(__byte_perm(u, 0x4B400000u, 0x7651))),
-                  make_float2(kMagic + 128.0f, kMagic + 128.0f));
+    return make_float2(__uint_as_float(__byte_perm(u, 0x4B000000u, 0x7404)),
+                       __uint_as_float(__byte_perm(u, 0x4B000000u, 0x7414)));
 }
+constexpr float kI8Scale = 256.0f;
+constexpr float kI8OffsetOverScale = 32896.0f;  // (2^23 + 2^15) / 256
+
+// pass-1 bin 0 of T scaled samples (T c + 256 sum x, exact) -> sum x, exactly
+template <int T>
+__device__ __forceinline__ float2 kOffsetFix(float2 v) {
+    constexpr float k = -(float)T * kI8OffsetOverScale;
+    return f2_fma(v, make_float2(1.0f / kI8Scale, 1.0f / kI8Scale), make_float2(k, k));
+}
+
+// 16-byte global -> shared copy that bypasses the registers (cp.async, L2 only)
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Front-end features of one F-engine instantiation: none, or delay compensation
 // (an integer advance of the frames and / or the per-channel fractional phase).
@@ -129,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
                                                       double *__restrict__ power, int n_in, int K,
                                                       const float2 *__restrict__ tw_glob, int i0, int vec_out,
                                                       const int *__restrict__ dint,
-                                                      const float2 *__restrict__ dph) {
+                                                      const float2 *__restrict__ dph, int async_raw) {
     using C = FCfg<N, I8, MODE>;
     constexpr int T = C::T, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
     constexpr bool DLY = FEAT == kDelay;  // delay code compiled in
@@ -148,6 +171,25 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
 
     const int i = i0 + blockIdx.y;
     const int a0 = blockIdx.x * SB;
+    // Raw int8 frames without delays are copied asynchronously into the FFT's exchange
+    // buffer (free between exchanges): the copy for the next frame is issued after the
+    // current frame's exchange and lands while its pass 2 and re-packing run. Each of
+    // the T threads moves T / 8 16-byte pieces of the 2 N-byte frame.
+    constexpr bool kAsync = I8 && !DLY && T >= 8;
+    static_assert(!kAsync || sizeof(float) * C::GS >= 2 * N, "exchange buffer holds one raw frame");
+    const bool use_async = kAsync && async_raw;
+    // copy of frame s_ of this CTA into the exchange buffer of FFT slot s_ % G
+    auto issue_raw = [&](int s_) {
+        const int a_ = a0 + s_, t_ = threadIdx.x % T;
+        if (s_ < SB && a_ < K) {
+            const char *src = reinterpret_cast<const char *>(volt) + ((size_t)i * K + a_) * (size_t)N * 2;
+            char *dst = reinterpret_cast<char *>(ex + (size_t)(s_ % G) * C::GS);
+#pragma unroll
+            for (int c = 0; c < T / 8; ++c) cp_async16(dst + (c * T + t_) * 16, src + (c * T + t_) * 16);
+        }
+        cp_async_commit();
+    };
+    if (use_async) issue_raw(threadIdx.x / T);
     // Delay compensation: the frames are read D samples later in input i's stream
     // (samples outside the record are zero) and channel k = t + T k2 is multiplied by
     // c[t] d[k2] = exp(+j 2 pi k f / N): c is folded into the inter-pass twiddles
@@ -175,6 +217,7 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
             w = cmul(w, __ldg(dph + (size_t)i * 2 * T + m / T));  // table [k1][t]: c[k1]
             if (m < T) dsm[m] = __ldg(dph + (size_t)i * 2 * T + T + m);
         }
+        if constexpr (I8) w = make_float2(w.x * (1.0f / kI8Scale), w.y * (1.0f / kI8Scale));
         tws[m] = w;
         if constexpr (MODE == kPower) scs[m] = 0.0f;
     }
@@ -203,18 +246,25 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
         const bool inside = !DLY || (off >= 0 && off + N <= n_rec);
         if constexpr (I8) {
             const unsigned short *src = reinterpret_cast<const unsigned short *>(volt) + base;
-            if (inside) {
+            if (use_async) {
+                cp_async_wait_all();
+                __syncwarp();  // every lane's pieces of the frame have landed
+                const unsigned short *raw = reinterpret_cast<const unsigned short *>(exg) + t;
+#pragma unroll
+                for (int m = 0; m < T; ++m) v[m] = i8_to_f2_scaled(valid ? (uint32_t)raw[T * m] : 0u);
+                __syncwarp();  // read before the exchange overwrites the buffer
+            } else if (inside) {
 #pragma unroll
                 for (int m = 0; m < T; ++m) {
                     const uint32_t w = valid ? (uint32_t)__ldg(src + (size_t)T * m) : 0u;
-                    v[m] = i8_to_f2(w);
+                    v[m] = i8_to_f2_scaled(w);
                 }
             } else {
 #pragma unroll
                 for (int m = 0; m < T; ++m) {
                     const long long n = off + t + T * m;
                     const uint32_t w = (valid && n >= 0 && n < n_rec) ? (uint32_t)__ldg(src + (long long)T * m) : 0u;
-                    v[m] = i8_to_f2(w);
+                    v[m] = i8_to_f2_scaled(w);
                 }
             }
         } else {
@@ -230,7 +280,8 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
                 }
             }
         }
-        fft_dif<T>(v);  // v[bitrev(k1)] = Y[t][k1]
+        fft_dif<T>(v);  // v[bitrev(k1)] = Y[t][k1] (x 256, bin 0 offset, for int8 input)
+        if constexpr (I8) v[0] = kOffsetFix<T>(v[0]);
         sfor<0, T>([&](auto K1) {
             constexpr int k1 = decltype(K1)::value;
             // twiddle W_N^(t k1), table laid out [k1][t]
@@ -260,6 +311,7 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
             v[4 * j].y = r.x, v[4 * j + 1].y = r.y, v[4 * j + 2].y = r.z, v[4 * j + 3].y = r.w;
         }
         if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+        if (use_async && s0 + G < SB) issue_raw(s0 + G + g);  // next frame into the free buffer
         fft_dif<T>(v);  // v[bitrev(k2)] = X[t + T k2]
         if (valid) {
             sfor<0, T>([&](auto K2) {
@@ -367,8 +419,10 @@ corr_status launch_one_(const FShape &f, const void *volt, const float *scale, v
     // blockIdx.x (the spectra block) varies fastest, so the CTAs resident at one time
     // write neighbouring segments of the same output rows
     dim3 grid((f.n_spectra + C::SB - 1) / C::SB, f.n_run < 0 ? f.n_in : f.n_run);
+    // asynchronous raw copies need 16-byte aligned frames (2 N bytes each, N >= 64)
+    const int async_raw = reinterpret_cast<uintptr_t>(volt) % 16 == 0;
     kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw, f.i0, vec_out,
-                                          f.dint, f.dph);
+                                          f.dint, f.dph, async_raw);
     return check_launch("k_fengine");
 }
 

@@ -46,3 +46,17 @@ def test_single_process_aggregation():
 
     ms_step, rate = bench.job_time_and_rate(40.0, units_per_rank=2e9, steps=4, dist=None)
     assert ms_step == 10.0 and rate == pytest.approx(2e11)
+
+
+def test_fengine_fp32_rate():
+    """Nominal FFT arithmetic of the F-engine line: 5 N log2 N flop per FFT over
+    152 x 128 FP32 lanes x 2 flop at the sampled clock."""
+    import bench
+
+    r = bench.fengine_fp32_rate(1024, 2 * 2 ** 20, 4.0, {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0})
+    flop = 5 * 1024 * 10 * 2 * 2 ** 20
+    assert r["flop_per_launch"] == flop
+    assert r["achieved_tflops"] == pytest.approx(flop / 4e-3 / 1e12)
+    assert r["peak_tflops"] == pytest.approx(152 * 128 * 2 * 2.0e9 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved_tflops"] / r["peak_tflops"])
+    assert bench.fengine_fp32_rate(1024, 1, 1.0, None)["peak_tflops"] == pytest.approx(152 * 256 * 2.07e9 / 1e12)
