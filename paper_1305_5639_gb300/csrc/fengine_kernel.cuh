@@ -419,7 +419,8 @@ corr_status launch_one_(const FShape &f, const void *volt, const float *scale, v
     // blockIdx.x (the spectra block) varies fastest, so the CTAs resident at one time
     // write neighbouring segments of the same output rows
     dim3 grid((f.n_spectra + C::SB - 1) / C::SB, f.n_run < 0 ? f.n_in : f.n_run);
-    // asynchronous raw copies need 16-byte aligned frames (2 N bytes each, N >= 64)
+    // asynchronous raw copies need 16-byte aligned frames (2 N bytes each, N >= 64); the
+    // public entry points only accept 16-byte aligned voltages, so this is a safeguard
     const int async_raw = reinterpret_cast<uintptr_t>(volt) % 16 == 0;
     kern<<<grid, kThreads, C::smem, st>>>(volt, scale, out, power, f.n_in, f.n_spectra, f.tw, f.i0, vec_out,
                                           f.dint, f.dph, async_raw);

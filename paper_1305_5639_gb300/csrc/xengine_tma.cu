@@ -183,8 +183,42 @@ __device__ __forceinline__ void decode(long long item, int n_tiles, int &chan, i
     bj = t - r * (r + 1) / 2;
 }
 
+// 16-warp epilogues (wide INT8 and short-time INT8): write one warp's INT32 sums of a
+// tile (rows wq * 32 + lane, columns 32 qc .. 32 qc + 31; Re in R[x], Im in R[32 + x])
+// into the packed accumulator through the warp's 2 KB shared-memory slice, 8 columns
+// at a time, so that 8 lanes write one row's 64 contiguous bytes.
+__device__ __forceinline__ void write_sums16(const int (&R)[64], const Item &itm, unsigned char *slice, int wq,
+                                             int qc, int lane, int store) {
+    int2 *sl = reinterpret_cast<int2 *>(slice);
+    int2 *acc = static_cast<int2 *>(itm.acc);
+    const long long rbase = (long long)itm.chan * itm.B;
+    const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
+#pragma unroll
+    for (int sc = 0; sc < 4; ++sc) {
+#pragma unroll
+        for (int x = 0; x < 8; ++x) sl[lane * 8 + ((x + lane) & 7)] = make_int2(R[8 * sc + x], R[32 + 8 * sc + x]);
+        __syncwarp();
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const int r = rr * 4 + (lane >> 3), e = lane & 7;
+            const int ii = I0 + wq * 32 + r, jj = J0 + 32 * qc + 8 * sc + e;
+            if (ii < itm.n_in && jj <= ii) {
+                int2 *dst = acc + rbase + (long long)ii * (ii + 1) / 2 + jj;
+                int2 v = sl[r * 8 + ((e + r) & 7)];
+                if (!store) {
+                    const int2 o = *dst;
+                    v.x += o.x;
+                    v.y += o.y;
+                }
+                *dst = v;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 template <int MODE, class C, bool ST = false, bool WIDE = false>
-__global__ void __launch_bounds__(WIDE ? NTHREADS_WIDE : NTHREADS, 1) k_xeng_tma(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WIDE : NTHREADS, 1) k_xeng_tma(const __grid_constant__ CUtensorMap tmap,
                                                           const __grid_constant__ CUtensorMap tmapB, const TParams p) {
     constexpr int KB = C::KB, NPL = C::NPL, PLANE = C::PLANE, STAGE_BYTES = C::STAGE_BYTES;
     constexpr int CHUNK_KB = C::CHUNK_KB, OFF_OSTG = C::OFF_OSTG, OFF_BAR = C::OFF_BAR;
@@ -195,7 +229,10 @@ __global__ void __launch_bounds__(WIDE ? NTHREADS_WIDE : NTHREADS, 1) k_xeng_tma
     // D2 sums one kind of product, |.| <= 127^2 per spectrum, so 1024-spectrum FP32 chunks
     // stay exact; D1 and D2 fill TMEM, so the accumulator is single-buffered.
     constexpr bool W = WIDE && MODE == kInt8 && NPL == 2 && !ST;
-    constexpr int CHUNK = MODE == kInt8 ? (W ? 2 * CHUNK_KB : CHUNK_KB) : 0;
+    // short-time INT8: the narrow, double-buffered accumulator drained by 16 epilogue
+    // warps (warps 4..19), each owning 32 columns of Re V and Im V for 32 rows
+    constexpr bool S16 = ST && MODE == kInt8 && NPL == 2 && !WIDE;
+    constexpr int CHUNK = W ? 2 * CHUNK_KB : CHUNK_KB;  // INT8 fold period in stages (unused by FP16 and the adjoint)
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -218,7 +255,7 @@ __global__ void __launch_bounds__(WIDE ? NTHREADS_WIDE : NTHREADS, 1) k_xeng_tma
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(accf_bar(b), 1);
-            tc::mbar_init(acce_bar(b), W ? 2 * NEPI : NEPI);
+            tc::mbar_init(acce_bar(b), (W || S16) ? 2 * NEPI : NEPI);
         }
         tc::mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -370,11 +407,9 @@ __global__ void __launch_bounds__(WIDE ? NTHREADS_WIDE : NTHREADS, 1) k_xeng_tma
         bool alive = true;
         for (long long it = 0; it < my_items && alive; ++it) {
             const Item itm = get_item(p, &tmap, it);
-            const int chan = itm.chan;
-            const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
             const int nkb = (itm.K + KB - 1) / KB;
             const int chunks = (nkb + CHUNK - 1) / CHUNK;
-            int R[64];  // INT32 sums: Re of j = J0 + 32 qc + x in R[x], Im in R[32 + x]
+            int R[64];  // INT32 sums: Re of column 32 qc + x in R[x], Im in R[32 + x]
 #pragma unroll
             for (int x = 0; x < 64; ++x) R[x] = 0;
             for (int c = 0; c < chunks; ++c) {
@@ -406,35 +441,79 @@ __global__ void __launch_bounds__(WIDE ? NTHREADS_WIDE : NTHREADS, 1) k_xeng_tma
                 tc::mbar_arrive(acce_bar(0));
             }
             if (!alive) break;
-            // write the tile's INT32 sums through the warp's 2 KB shared-memory slice,
-            // 8 columns at a time, so that 8 lanes write one row's 64 contiguous bytes
-            int2 *sl = reinterpret_cast<int2 *>(sgen + OFF_OSTG + ew * (OSTG_WARP / 2));
-            int2 *acc = static_cast<int2 *>(itm.acc);
-            const long long rbase = (long long)chan * itm.B;
-#pragma unroll
-            for (int sc = 0; sc < 4; ++sc) {
-#pragma unroll
-                for (int x = 0; x < 8; ++x) sl[lane * 8 + ((x + lane) & 7)] = make_int2(R[8 * sc + x], R[32 + 8 * sc + x]);
-                __syncwarp();
-#pragma unroll
-                for (int rr = 0; rr < 8; ++rr) {
-                    const int r = rr * 4 + (lane >> 3), e = lane & 7;
-                    const int ii = I0 + wq * 32 + r, jj = J0 + 32 * qc + 8 * sc + e;
-                    if (ii < itm.n_in && jj <= ii) {
-                        int2 *dst = acc + rbase + (long long)ii * (ii + 1) / 2 + jj;
-                        int2 v = sl[r * 8 + ((e + r) & 7)];
-                        if (!p.store) {
-                            const int2 o = *dst;
-                            v.x += o.x;
-                            v.y += o.y;
-                        }
-                        *dst = v;
-                    }
-                }
-                __syncwarp();
-            }
+            write_sums16(R, itm, sgen + OFF_OSTG + ew * (OSTG_WARP / 2), wq, qc, lane, p.store);
         }
-    } else if (warp >= 4) {
+    } else if (S16 && warp >= 4) {
+        // ------------------------------------------------------------ short-time INT8 epilogue
+        // 16 warps, four per TMEM lane quarter, each owning columns [32 qc, 32 qc + 32) of
+        // Re V and Im V for its 32 rows. Every chunk (one short-time block, <= 512 spectra,
+        // exact in FP32) is converted, added into the INT32 integration sums and written
+        // as the block's visibilities: 16 columns at a time through the warp's 2 KB slice,
+        // so that 16 lanes then write one row's 64 contiguous bytes.
+        const int ew = warp - 4;               // 0..15
+        const int wq = warp & 3;               // TMEM lane quarter this warp may access
+        const int qc = ew >> 2;                // column quarter
+        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+        int *sl = reinterpret_cast<int *>(sgen + OFF_OSTG + ew * (OSTG_WARP / 2));  // [32 rows][16]
+        uint32_t af_phase[2] = {0, 0};
+        long long ch = 0;
+        bool alive = true;
+        for (long long it = 0; it < my_items && alive; ++it) {
+            const Item itm = get_item(p, &tmap, it);
+            const int chan = itm.chan;
+            const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
+            const int nkb = (itm.K + KB - 1) / KB;
+            const int chunks = (nkb + p.st_kb - 1) / p.st_kb;
+            // (row offsets ii (ii + 1) / 2 below: one channel's triangle has < 2^32 entries)
+            int R[64];  // INT32 sums: Re of j = J0 + 32 qc + x in R[x], Im in R[32 + x]
+#pragma unroll
+            for (int x = 0; x < 64; ++x) R[x] = 0;
+            for (int c = 0; c < chunks; ++c, ++ch) {
+                const int buf = (int)(ch & 1);
+                if (!tc::mbar_wait(accf_bar(buf), af_phase[buf], abort_flag, p.status)) {
+                    alive = false;
+                    break;
+                }
+                af_phase[buf] ^= 1u;
+                tc::tc_fence_after();
+                const uint32_t d = tmem + lane_off + (uint32_t)(buf * 256) + (uint32_t)(32 * qc);
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    // cb 0, 1: Re columns 32 qc + 16 cb; cb 2, 3: Im columns 128 + 32 qc + 16 (cb - 2),
+                    // read from TMEM 8 columns at a time (register budget of 640 threads)
+#pragma unroll
+                    for (int hf = 0; hf < 2; ++hf) {
+                        uint32_t v[8];
+                        tc::tmem_ld8(d + (cb < 2 ? 0u : 128u) + 16u * (cb & 1) + 8u * hf, v);
+                        tc::tmem_wait_ld();
+                        // row `lane`, column y at word lane * 16 + ((y + lane / 2) & 15): the writes
+                        // of one y and the 16-word row reads below are free of bank conflicts
+#pragma unroll
+                        for (int x = 0; x < 8; ++x) {
+                            const int qx = __float2int_rn(__uint_as_float(v[x]));
+                            R[16 * cb + 8 * hf + x] += qx;
+                            sl[lane * 16 + ((8 * hf + x + (lane >> 1)) & 15)] = qx;
+                        }
+                    }
+                    __syncwarp();
+                    const int jb = J0 + 32 * qc + 16 * (cb & 1);
+                    int *plane = p.st_out + ((long long)(c * p.st_nchan + chan) * 2 + (cb >> 1)) * itm.B;
+#pragma unroll 4
+                    for (int rr = 0; rr < 16; ++rr) {
+                        const int r = rr * 2 + (lane >> 4), e = lane & 15;
+                        const int ii = I0 + wq * 32 + r, jj = jb + e;
+                        const uint32_t ro = (uint32_t)(((unsigned long long)ii * (unsigned)(ii + 1)) >> 1);
+                        if (ii < itm.n_in && jj <= ii) plane[ro + jj] = sl[r * 16 + ((e + (r >> 1)) & 15)];
+                    }
+                    __syncwarp();
+                }
+                tc::tc_fence_before();
+                tc::mbar_arrive(acce_bar(buf));
+            }
+            if (!alive) break;
+            write_sums16(R, itm, reinterpret_cast<unsigned char *>(sl), wq, qc, lane, p.store);
+        }
+    } else if (!W && !S16 && warp >= 4) {
         // ------------------------------------------------------------ epilogue
         const int ew = warp - 4;               // 0..7
         const int wq = warp & 3;               // TMEM lane quarter this warp may access
@@ -450,8 +529,7 @@ __global__ void __launch_bounds__(WIDE ? NTHREADS_WIDE : NTHREADS, 1) k_xeng_tma
             const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
             const int i = I0 + m;
             const int nkb = (itm.K + KB - 1) / KB;
-            const int chunk_kb = ST ? p.st_kb : CHUNK;
-            const int chunks_per_item = MODE == kInt8 ? (nkb + chunk_kb - 1) / chunk_kb : 1;
+            const int chunks_per_item = MODE == kInt8 ? (nkb + CHUNK - 1) / CHUNK : 1;
             if constexpr (MODE == kInt8) {
                 int R[128];  // INT32 sums: Re of j = J0 + 64h + x in R[x], Im in R[64 + x]
 #pragma unroll
@@ -471,29 +549,8 @@ __global__ void __launch_bounds__(WIDE ? NTHREADS_WIDE : NTHREADS, 1) k_xeng_tma
                         uint32_t v[16];
                         tc::tmem_ld16(d + (cb < 4 ? 0u : 128u) + 16u * (cb & 3), v);
                         tc::tmem_wait_ld();
-                        // short-time block c of this tile (ST): the 16 columns of the warp's 32
-                        // rows go through the warp's output slice, so that 16 lanes then write
-                        // one row's 64 contiguous bytes
-                        int *sl = reinterpret_cast<int *>(sgen + OFF_OSTG + ew * OSTG_WARP);
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) {
-                            const int qx = __float2int_rn(__uint_as_float(v[x]));
-                            R[16 * cb + x] += qx;
-                            if constexpr (ST) sl[lane * 16 + ((x + lane) & 15)] = qx;
-                        }
-                        if constexpr (ST) {
-                            __syncwarp();
-                            const int jb = J0 + 64 * h + 16 * (cb & 3);
-                            int *plane = p.st_out + ((long long)(c * p.st_nchan + chan) * 2 + (cb >> 2)) * itm.B;
-#pragma unroll 1
-                            for (int rr = 0; rr < 16; ++rr) {
-                                const int r = rr * 2 + (lane >> 4), e = lane & 15;
-                                const int ii = I0 + wq * 32 + r, jj = jb + e;
-                                if (ii < itm.n_in && jj <= ii)
-                                    plane[(long long)ii * (ii + 1) / 2 + jj] = sl[r * 16 + ((e + r) & 15)];
-                            }
-                            __syncwarp();
-                        }
+                        for (int x = 0; x < 16; ++x) R[16 * cb + x] += __float2int_rn(__uint_as_float(v[x]));
                     }
                     tc::tc_fence_before();
                     tc::mbar_arrive(acce_bar(buf));
@@ -809,7 +866,7 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
         using C = TCfg<2, 64>;
         auto kern = k_xeng_tma<kInt8, C, true>;
         CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        kern<<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+        kern<<<grid, NTHREADS_WIDE, C::SMEM_BYTES, st>>>(tmap, tmap, p);
     } else if (h.precision == CORR_PREC_INT8) {
         using C = TCfg<2, 64>;
         if (kInt8Wide && !p.vis64) {

@@ -60,6 +60,22 @@ def test_fengine_int8_requant_corner_turn(cuda_ok, N, n_ant, n_pol, K):
     c.close()
 
 
+def test_fengine_unaligned_input_rejected(cuda_ok):
+    """Raw voltages must start on a 16-byte boundary (the F-engine copies whole
+    frames asynchronously in 16-byte pieces): an offset view is refused."""
+    N, K = 1024, 8
+    v = torch.zeros((2, K * N, 2), dtype=torch.int8, device=DEV)
+    raw = torch.empty(v.numel() + 16, dtype=torch.uint8, device=DEV)
+    vu = raw[2:2 + v.numel()].view(torch.int8).view(v.shape)
+    c = api.Correlator(2, 1, N, K, precision="int8", planar=True)
+    sc = torch.ones(N, device=DEV)
+    for call in (lambda: c.fengine(vu, sc), lambda: c.fengine_power(vu)):
+        with pytest.raises(CorrError) as e:
+            call()
+        assert e.value.status == CORR_EINVAL
+    c.close()
+
+
 def test_fengine_power(cuda_ok):
     n_in, N, K = 4, 256, 24
     v = synth.volt_fp32(n_in, N, K, seed=5)
