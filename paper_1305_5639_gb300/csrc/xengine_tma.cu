@@ -52,7 +52,6 @@ namespace {
 
 constexpr int TILE = 128;
 constexpr int NSTAGE = 3;
-constexpr bool kInt8Wide = true;  // INT8 triangle launches use the wide (N = 256) MMA form
 constexpr int NEPI = 256;                 // epilogue threads (warps 4..11)
 constexpr int NTHREADS = 384;
 constexpr int NTHREADS_WIDE = 640;        // wide INT8 form: 16 epilogue warps (warps 4..19)
@@ -184,15 +183,48 @@ __device__ __forceinline__ void decode(long long item, int n_tiles, int &chan, i
 }
 
 // 16-warp epilogues (wide INT8 and short-time INT8): write one warp's INT32 sums of a
-// tile (rows wq * 32 + lane, columns 32 qc .. 32 qc + 31; Re in R[x], Im in R[32 + x])
-// into the packed accumulator through the warp's 2 KB shared-memory slice, 8 columns
-// at a time, so that 8 lanes write one row's 64 contiguous bytes.
-__device__ __forceinline__ void write_sums16(const int (&R)[64], const Item &itm, unsigned char *slice, int wq,
-                                             int qc, int lane, int store) {
+// tile (tile rows wq * 32 + lane, tile columns 32 qc .. 32 qc + 31; Re in R[x], Im in
+// R[32 + x]) through the warp's 2 KB shared-memory slice, so that consecutive lanes
+// write one row's contiguous bytes. Destinations: the packed INT32 accumulator (stored
+// or added; packed small sub-arrays map tile rows and columns to (channel, input)
+// through lg_npad), the cross-only rectangle, or the FP64 long integration (added).
+__device__ __forceinline__ void write_sums16(const int (&R)[64], const Item &itm, const TParams &p,
+                                             unsigned char *slice, int wq, int qc, int lane) {
+    const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
+    const long long rbase = (long long)itm.chan * itm.B;
+    if (p.vis64) {
+        // 4 double2 per row slice: 32 rows x 64 B, 4 lanes per row; all reads of a round in
+        // flight before its writes
+        double2 *sl = reinterpret_cast<double2 *>(slice);
+#pragma unroll
+        for (int sc = 0; sc < 8; ++sc) {
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                sl[lane * 4 + ((x + lane) & 3)] = make_double2((double)R[4 * sc + x], (double)R[32 + 4 * sc + x]);
+            __syncwarp();
+            double2 o[4];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const int r = rr * 8 + (lane >> 2), e = lane & 3;
+                const int ii = I0 + wq * 32 + r, jj = J0 + 32 * qc + 4 * sc + e;
+                o[rr] = (ii < itm.n_in && jj <= ii) ? __ldcg(p.vis64 + rbase + (long long)ii * (ii + 1) / 2 + jj)
+                                                    : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const int r = rr * 8 + (lane >> 2), e = lane & 3;
+                const int ii = I0 + wq * 32 + r, jj = J0 + 32 * qc + 4 * sc + e;
+                const double2 v = sl[r * 4 + ((e + r) & 3)];
+                if (ii < itm.n_in && jj <= ii)
+                    p.vis64[rbase + (long long)ii * (ii + 1) / 2 + jj] = make_double2(o[rr].x + v.x, o[rr].y + v.y);
+            }
+            __syncwarp();
+        }
+        return;
+    }
     int2 *sl = reinterpret_cast<int2 *>(slice);
     int2 *acc = static_cast<int2 *>(itm.acc);
-    const long long rbase = (long long)itm.chan * itm.B;
-    const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
+    const int msk = (1 << itm.lg_npad) - 1;
 #pragma unroll
     for (int sc = 0; sc < 4; ++sc) {
 #pragma unroll
@@ -201,11 +233,18 @@ __device__ __forceinline__ void write_sums16(const int (&R)[64], const Item &itm
 #pragma unroll
         for (int rr = 0; rr < 8; ++rr) {
             const int r = rr * 4 + (lane >> 3), e = lane & 7;
-            const int ii = I0 + wq * 32 + r, jj = J0 + 32 * qc + 8 * sc + e;
-            if (ii < itm.n_in && jj <= ii) {
-                int2 *dst = acc + rbase + (long long)ii * (ii + 1) / 2 + jj;
-                int2 v = sl[r * 8 + ((e + r) & 7)];
-                if (!store) {
+            const int tr = wq * 32 + r, tcl = 32 * qc + 8 * sc + e;  // tile row / column
+            const int q = tr >> itm.lg_npad, qcl = tcl >> itm.lg_npad;
+            const int ii = I0 + (tr & msk), jj = J0 + (tcl & msk);
+            const int2 v0 = sl[r * 8 + ((e + r) & 7)];
+            if (p.rect) {
+                // rectangle: tile row ii of group P, column jj of group Q
+                if (ii < p.n_p && jj < p.n_q)
+                    static_cast<int2 *>(p.rect_out)[((long long)itm.chan * p.n_p + ii) * p.n_q + jj] = v0;
+            } else if (q == qcl && itm.chan + q < itm.n_chan && ii < itm.n_in && jj <= ii) {
+                int2 *dst = acc + rbase + (long long)q * itm.B + (long long)ii * (ii + 1) / 2 + jj;
+                int2 v = v0;
+                if (!p.store) {
                     const int2 o = *dst;
                     v.x += o.x;
                     v.y += o.y;
@@ -441,7 +480,7 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
                 tc::mbar_arrive(acce_bar(0));
             }
             if (!alive) break;
-            write_sums16(R, itm, sgen + OFF_OSTG + ew * (OSTG_WARP / 2), wq, qc, lane, p.store);
+            write_sums16(R, itm, p, sgen + OFF_OSTG + ew * (OSTG_WARP / 2), wq, qc, lane);
         }
     } else if (S16 && warp >= 4) {
         // ------------------------------------------------------------ short-time INT8 epilogue
@@ -511,10 +550,10 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
                 tc::mbar_arrive(acce_bar(buf));
             }
             if (!alive) break;
-            write_sums16(R, itm, reinterpret_cast<unsigned char *>(sl), wq, qc, lane, p.store);
+            write_sums16(R, itm, p, reinterpret_cast<unsigned char *>(sl), wq, qc, lane);
         }
     } else if (!W && !S16 && warp >= 4) {
-        // ------------------------------------------------------------ epilogue
+        // ------------------------------------------------------------ epilogue (FP16, adjoint)
         const int ew = warp - 4;               // 0..7
         const int wq = warp & 3;               // TMEM lane quarter this warp may access
         const int h = ew >> 2;                 // column half: j in [64 h, 64 h + 64)
@@ -528,107 +567,7 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
             const int chan = itm.chan;
             const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
             const int i = I0 + m;
-            const int nkb = (itm.K + KB - 1) / KB;
-            const int chunks_per_item = MODE == kInt8 ? (nkb + CHUNK - 1) / CHUNK : 1;
-            if constexpr (MODE == kInt8) {
-                int R[128];  // INT32 sums: Re of j = J0 + 64h + x in R[x], Im in R[64 + x]
-#pragma unroll
-                for (int x = 0; x < 128; ++x) R[x] = 0;
-                for (int c = 0; c < chunks_per_item; ++c, ++ch) {
-                    const int buf = (int)(ch & 1);
-                    if (!tc::mbar_wait(accf_bar(buf), af_phase[buf], abort_flag, p.status)) {
-                        alive = false;
-                        break;
-                    }
-                    af_phase[buf] ^= 1u;
-                    tc::tc_fence_after();
-                    const uint32_t d = tmem + lane_off + (uint32_t)(buf * 256) + (uint32_t)(64 * h);
-#pragma unroll
-                    for (int cb = 0; cb < 8; ++cb) {
-                        // cb < 4: Re columns 64h + 16 cb; cb >= 4: Im columns 128 + 64h + 16 (cb - 4)
-                        uint32_t v[16];
-                        tc::tmem_ld16(d + (cb < 4 ? 0u : 128u) + 16u * (cb & 3), v);
-                        tc::tmem_wait_ld();
-#pragma unroll
-                        for (int x = 0; x < 16; ++x) R[16 * cb + x] += __float2int_rn(__uint_as_float(v[x]));
-                    }
-                    tc::tc_fence_before();
-                    tc::mbar_arrive(acce_bar(buf));
-                }
-                if (!alive) break;
-                // write the tile's INT32 sums through a per-warp shared-memory slice so that
-                // every global row segment is written (or read-modify-written) contiguously
-                unsigned char *ostg = sgen + OFF_OSTG + ew * OSTG_WARP;
-                const long long rbase = (long long)chan * itm.B;
-                if (p.vis64) {
-                    // 8 double2 per row slice: 32 rows x 128 B
-                    double2 *sl = reinterpret_cast<double2 *>(ostg);
-#pragma unroll
-                    for (int sc = 0; sc < 8; ++sc) {
-#pragma unroll
-                        for (int x = 0; x < 8; ++x)
-                            sl[lane * 8 + ((x + lane) & 7)] = make_double2((double)R[8 * sc + x], (double)R[64 + 8 * sc + x]);
-                        __syncwarp();
-                        // all eight row reads in flight before any write (latency, not bandwidth,
-                        // bounds this read-modify-write)
-                        double2 o[8];
-#pragma unroll
-                        for (int rr = 0; rr < 8; ++rr) {
-                            const int r = rr * 4 + (lane >> 3), e = lane & 7;
-                            const int ii = I0 + wq * 32 + r, jj = J0 + 64 * h + 8 * sc + e;
-                            o[rr] = (ii < itm.n_in && jj <= ii)
-                                        ? __ldcg(p.vis64 + rbase + (long long)ii * (ii + 1) / 2 + jj)
-                                        : make_double2(0.0, 0.0);
-                        }
-#pragma unroll
-                        for (int rr = 0; rr < 8; ++rr) {
-                            const int r = rr * 4 + (lane >> 3), e = lane & 7;
-                            const int ii = I0 + wq * 32 + r, jj = J0 + 64 * h + 8 * sc + e;
-                            const double2 v = sl[r * 8 + ((e + r) & 7)];
-                            if (ii < itm.n_in && jj <= ii)
-                                p.vis64[rbase + (long long)ii * (ii + 1) / 2 + jj] =
-                                    make_double2(o[rr].x + v.x, o[rr].y + v.y);
-                        }
-                        __syncwarp();
-                    }
-                } else {
-                    // 16 int2 per row slice: 32 rows x 128 B
-                    int2 *sl = reinterpret_cast<int2 *>(ostg);
-                    int2 *acc = static_cast<int2 *>(itm.acc);
-#pragma unroll
-                    for (int sc = 0; sc < 4; ++sc) {
-#pragma unroll
-                        for (int x = 0; x < 16; ++x)
-                            sl[lane * 16 + ((x + lane) & 15)] = make_int2(R[16 * sc + x], R[64 + 16 * sc + x]);
-                        __syncwarp();
-#pragma unroll
-                        for (int rr = 0; rr < 16; ++rr) {
-                            const int r = rr * 2 + (lane >> 4), e = lane & 15;
-                            // tile row / column -> (channel, input) through the channel packing
-                            const int tr = wq * 32 + r, tcl = 64 * h + 16 * sc + e;
-                            const int q = tr >> itm.lg_npad, qc = tcl >> itm.lg_npad;
-                            const int msk = (1 << itm.lg_npad) - 1;
-                            const int ii = I0 + (tr & msk), jj = J0 + (tcl & msk);
-                            if (p.rect) {
-                                // rectangle: tile row ii of group P, column jj of group Q
-                                if (ii < p.n_p && jj < p.n_q)
-                                    static_cast<int2 *>(p.rect_out)[((long long)chan * p.n_p + ii) * p.n_q + jj] =
-                                        sl[r * 16 + ((e + r) & 15)];
-                            } else if (q == qc && chan + q < itm.n_chan && ii < itm.n_in && jj <= ii) {
-                                int2 *dst = acc + rbase + (long long)q * itm.B + (long long)ii * (ii + 1) / 2 + jj;
-                                int2 v = sl[r * 16 + ((e + r) & 15)];
-                                if (!p.store) {
-                                    const int2 o = *dst;
-                                    v.x += o.x;
-                                    v.y += o.y;
-                                }
-                                *dst = v;
-                            }
-                        }
-                        __syncwarp();
-                    }
-                }
-            } else if constexpr (MODE == kAdj) {
+            if constexpr (MODE == kAdj) {
                 // dX = conj(g_m) Y and sum_a conj(X_ma) Y_ma over this thread's 64 spectra,
                 // Y = 2^-e_f D (rows m = i, columns a = J0 + 64 h + ...)
                 const int buf = (int)(ch & 1);
@@ -797,9 +736,17 @@ corr_status tma_encode_planar(void *tmap128, const void *planes, int n_in, int n
     return CORR_OK;
 }
 
+// Every INT8 launch but the short-time one: the wide form, 640 threads.
+corr_status launch_int8_wide(const CUtensorMap &tmap, const TParams &p, unsigned grid, cudaStream_t st) {
+    using C = TCfg<2, 64>;
+    auto kern = k_xeng_tma<kInt8, C, false, true>;
+    CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+    kern<<<grid, NTHREADS_WIDE, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+    return CORR_OK;
+}
+
 corr_status launch_xengine_tma_batch(const void *d_tmaps, const BatchSub *d_subs, const int4 *d_items,
                                      const int *d_cta_off, int grid, int *status, cudaStream_t st) {
-    using C = TCfg<2, 64>;
     TParams p{};
     p.tmaps = static_cast<const CUtensorMap *>(d_tmaps);
     p.subs = d_subs;
@@ -809,8 +756,8 @@ corr_status launch_xengine_tma_batch(const void *d_tmaps, const BatchSub *d_subs
     p.status = status;
     p.store = 1;
     CUtensorMap dummy{};  // unused in batched mode (each item names its sub's map)
-    CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-    k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(dummy, dummy, p);
+    const corr_status s = launch_int8_wide(dummy, p, (unsigned)grid, st);
+    if (s != CORR_OK) return s;
     return check_launch("k_xeng_tma (batched)");
 }
 
@@ -868,15 +815,8 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
         CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
         kern<<<grid, NTHREADS_WIDE, C::SMEM_BYTES, st>>>(tmap, tmap, p);
     } else if (h.precision == CORR_PREC_INT8) {
-        using C = TCfg<2, 64>;
-        if (kInt8Wide && !p.vis64) {
-            auto kern = k_xeng_tma<kInt8, C, false, true>;
-            CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-            kern<<<grid, NTHREADS_WIDE, C::SMEM_BYTES, st>>>(tmap, tmap, p);
-        } else {
-            CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-            k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
-        }
+        const corr_status s = launch_int8_wide(tmap, p, grid, st);
+        if (s != CORR_OK) return s;
     } else if (npl == 2) {
         using C = TCfg<2, 64>;
         CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
@@ -931,9 +871,8 @@ corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl
     p.store = 1;
     const unsigned grid = (unsigned)(p.n_items < h.n_sm ? p.n_items : h.n_sm);
     if (h.precision == CORR_PREC_INT8) {
-        using C = TCfg<2, 64>;
-        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kInt8, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        k_xeng_tma<kInt8, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+        const corr_status s = launch_int8_wide(tmap, p, grid, st);
+        if (s != CORR_OK) return s;
     } else if (npl == 2) {
         using C = TCfg<2, 64>;
         CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
