@@ -63,6 +63,40 @@ def test_pfb_int8_requant(cuda_ok, planar):
     c.close()
 
 
+@pytest.mark.parametrize("N,n_ant,K,P,with_delays,planar", [(1024, 2, 16, 3, True, True), (256, 3, 21, 5, True, False),
+                                                              (64, 2, 24, 8, False, True), (16, 2, 30, 1, True, False)])
+def test_pfb_int8_fused_taps_and_delays(cuda_ok, N, n_ant, K, P, with_delays, planar):
+    """int8 voltages through the filter bank and the re-packing: tap counts that are
+    not a multiple of 4, delays (advance past both ends of the record, fractional
+    phase) and both output layouts against the oracle's definition."""
+    n_pol = 2
+    n_in = n_ant * n_pol
+    v = synth.volt_int8(n_ant, n_pol, N, K, seed=N + P)
+    h = _sinc_hann(P, N)
+    d = None
+    if with_delays:
+        d = np.random.default_rng(P).uniform(-1.5 * N, 1.5 * N, n_in).astype(np.float32)
+        d[0] = 0.0
+    c = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=planar)
+    c.set_pfb(h)
+    if with_delays:
+        c.set_delays(d)
+    S = oracle.channelise_pfb(v, N, h, delays=d)
+    scale = (16.0 / np.sqrt(np.mean(np.abs(S) ** 2, axis=(1, 2)) / 2)).astype(np.float32)
+    out = c.fengine(torch.from_numpy(v).to(DEV), torch.from_numpy(scale).to(DEV)).cpu().numpy()
+    if planar:
+        out = np.transpose(out, (0, 2, 3, 1)).astype(np.int8)
+    q, margin = oracle.requant(S, scale)
+    eps = 8 * np.log2(N) * max(P, 2) * 2.0 ** -24 * np.sqrt(np.mean(np.abs(S) ** 2)) * scale.max() * 8
+    sure = margin > eps
+    assert sure.mean() > 0.9
+    assert np.array_equal(out[sure], q[sure])
+    assert np.all(np.abs(out.astype(np.int32) - q.astype(np.int32)) <= 1)
+    p_gpu = c.fengine_power(torch.from_numpy(v).to(DEV)).cpu().numpy()
+    assert np.allclose(p_gpu, oracle.channel_power(S), rtol=1e-4)
+    c.close()
+
+
 def test_pfb_tone_leakage(cuda_ok):
     """A tone halfway between two bins leaks far less into distant channels through
     the 4-tap filter bank than through the plain FFT (the filter bank's purpose),
