@@ -109,6 +109,15 @@ __device__ __forceinline__ void ob_codes_to_f16_planes(uint32_t u, uint32_t &re,
     im = *reinterpret_cast<uint32_t *>(&m);
 }
 
+// complex int8 sample (16 bits: re in the low byte) -> float2, exactly:
+// (0x4B400000 | (x + 128)) is the float 12582912 + x + 128.
+__device__ __forceinline__ float2 i8_to_f2(uint32_t w) {
+    const uint32_t u = w ^ 0x8080u;
+    return f2_sub(make_float2(__uint_as_float(__byte_perm(u, 0x4B400000u, 0x7650)),
+                              __uint_as_float(__byte_perm(u, 0x4B400000u, 0x7651))),
+                  make_float2(kMagic + 128.0f, kMagic + 128.0f));
+}
+
 // complex int8 sample x (16 bits: re in the low byte) -> float2 (c + 256 re, c + 256 im)
 // with the constant c = 2^23 + 2^15, exactly: the float with bits 0x4B00 (x + 128) 00
 // is 2^23 + 256 (x + 128). The offset needs no subtraction here: the first radix-2
@@ -156,6 +165,9 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
     using C = FCfg<N, I8, MODE>;
     constexpr int T = C::T, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
     constexpr bool DLY = FEAT == kDelay;  // delay code compiled in
+    // int8 samples enter the plain FFT scaled by 256 on an offset (i8_to_f2_scaled); the
+    // delay instantiation converts them exactly (measured faster there)
+    constexpr bool SCALED = I8 && !DLY;
     // the integer advance and the phase are separate: the filter-bank path applies the
     // advance in its FIR pass and only the phase here
     const bool has_shift = DLY && dint != nullptr, has_dly = DLY && dph != nullptr;
@@ -217,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
             w = cmul(w, __ldg(dph + (size_t)i * 2 * T + m / T));  // table [k1][t]: c[k1]
             if (m < T) dsm[m] = __ldg(dph + (size_t)i * 2 * T + T + m);
         }
-        if constexpr (I8) w = make_float2(w.x * (1.0f / kI8Scale), w.y * (1.0f / kI8Scale));
+        if constexpr (SCALED) w = make_float2(w.x * (1.0f / kI8Scale), w.y * (1.0f / kI8Scale));
         tws[m] = w;
         if constexpr (MODE == kPower) scs[m] = 0.0f;
     }
@@ -257,14 +269,14 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
 #pragma unroll
                 for (int m = 0; m < T; ++m) {
                     const uint32_t w = valid ? (uint32_t)__ldg(src + (size_t)T * m) : 0u;
-                    v[m] = i8_to_f2_scaled(w);
+                    v[m] = SCALED ? i8_to_f2_scaled(w) : i8_to_f2(w);
                 }
             } else {
 #pragma unroll
                 for (int m = 0; m < T; ++m) {
                     const long long n = off + t + T * m;
                     const uint32_t w = (valid && n >= 0 && n < n_rec) ? (uint32_t)__ldg(src + (long long)T * m) : 0u;
-                    v[m] = i8_to_f2_scaled(w);
+                    v[m] = SCALED ? i8_to_f2_scaled(w) : i8_to_f2(w);
                 }
             }
         } else {
@@ -281,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
             }
         }
         fft_dif<T>(v);  // v[bitrev(k1)] = Y[t][k1] (x 256, bin 0 offset, for int8 input)
-        if constexpr (I8) v[0] = kOffsetFix<T>(v[0]);
+        if constexpr (SCALED) v[0] = kOffsetFix<T>(v[0]);
         sfor<0, T>([&](auto K1) {
             constexpr int k1 = decltype(K1)::value;
             // twiddle W_N^(t k1), table laid out [k1][t]
