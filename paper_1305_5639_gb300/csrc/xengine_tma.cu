@@ -16,19 +16,20 @@
 // 512 spectra, the epilogue converts the other exactly and adds it into INT32
 // running sums held in registers. The result is bit-exact.
 //
-// INT8 triangle launches use the wide form instead (the kernel's WIDE variant):
-// two N = 256 MMAs per 16 spectra, D1 += re_I [re_J; im_J]^T and
-// D2 += im_I [re_J; im_J]^T, with Re V = D1a + D2b and Im V = D2a - D1b formed in
-// INT32 by the epilogue; it reads 25% fewer operand bytes from shared memory per
-// product (the narrow form's limit), folds every 1024 spectra (each half of D1, D2
-// sums one kind of product) and, D1 and D2 filling TMEM, single-buffers the
-// accumulator.
+// The INT8 and FP16 launches (triangle, rectangle, batched sub-arrays) use the wide
+// form instead (the kernel's WIDE variant): two N = 256 MMAs per 16 spectra (six for
+// hi/lo), D1 += re_I [re_J; im_J]^T and D2 += im_I [re_J; im_J]^T, with
+// Re V = D1a + D2b and Im V = D2a - D1b formed by the epilogue (in INT32 for INT8, in
+// FP32 for FP16); it reads 25% fewer operand bytes from shared memory per product (the
+// narrow form's limit), and, D1 and D2 filling TMEM, single-buffers the accumulator.
+// INT8 folds every 1024 spectra (each half of D1, D2 sums one kind of product). The
+// narrow, double-buffered form remains for the short-time INT8 output and the adjoint.
 //
-// Warp roles (one persistent CTA per SM; 384 threads, 640 in the wide form):
+// Warp roles (one persistent CTA per SM; 384 threads for the adjoint, 640 otherwise):
 //   warp 0       TMA producer (one thread): 3-stage ring of 64-spectrum stages
 //   warp 1       TMEM allocator + single-thread MMA issuer
-//   warps 4-11   epilogue, two warps per TMEM lane quarter, each owning half of
-//                the tile's columns and their INT32 sums (wide form: warps 4-19,
+//   warps 4-11   adjoint epilogue, two warps per TMEM lane quarter, each owning half
+//                of the tile's columns (wide form and short-time INT8: warps 4-19,
 //                four per lane quarter, a quarter of the columns each)
 // Every mbarrier wait is bounded; on time-out the CTA records CORR_ETIMEOUT and
 // every role leaves its loop.
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
     // the epilogue forms Re V = D1a + D2b and Im V = D2a - D1b in INT32. Each half of D1,
     // D2 sums one kind of product, |.| <= 127^2 per spectrum, so 1024-spectrum FP32 chunks
     // stay exact; D1 and D2 fill TMEM, so the accumulator is single-buffered.
-    constexpr bool W = WIDE && MODE == kInt8 && NPL == 2 && !ST;
+    constexpr bool W = WIDE && ((MODE == kInt8 && NPL == 2) || MODE == kFp16) && !ST;
     // short-time INT8: the narrow, double-buffered accumulator drained by 16 epilogue
     // warps (warps 4..19), each owning 32 columns of Re V and Im V for 32 rows
     constexpr bool S16 = ST && MODE == kInt8 && NPL == 2 && !WIDE;
@@ -415,6 +416,14 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
                             const uint64_t bb = C::desc(b0 + ko);  // [Re_J; Im_J], 256 rows
                             tc::mma_f16(d_re, C::desc(a0 + ko), bb, ID256, acc);
                             tc::mma_f16(d_im, C::desc(a0 + PLANE + ko), bb, ID256, acc);
+                            if constexpr (NPL == 4) {
+                                // hi/lo: h l and l h into the same accumulators
+                                const uint64_t bl = C::desc(b0 + 2 * PLANE + ko);  // [Re_Jl; Im_Jl]
+                                tc::mma_f16(d_re, C::desc(a0 + ko), bl, ID256, 1u);
+                                tc::mma_f16(d_im, C::desc(a0 + PLANE + ko), bl, ID256, 1u);
+                                tc::mma_f16(d_re, C::desc(a0 + 2 * PLANE + ko), bb, ID256, 1u);
+                                tc::mma_f16(d_im, C::desc(a0 + 3 * PLANE + ko), bb, ID256, 1u);
+                            }
                         } else {
                             cmma(a0, b0, ko, (kin > 0 || k > 0) ? 1u : 0u);  // h h
                             if constexpr (NPL == 4) {
@@ -434,6 +443,104 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
             tc::mbar_wait(drain_bar, 0u, abort_flag, p.status, 1000000000ull, false);
         }
         __syncwarp();
+    } else if (W && MODE == kFp16 && warp >= 4) {
+        // ------------------------------------------------------------ wide FP16 epilogue
+        // 16 warps, four per TMEM lane quarter, each owning columns [32 qc, 32 qc + 32) of
+        // Re V = D1a + D2b and Im V = D2a - D1b for its 32 rows (FP32), drained once per
+        // tile from the single-buffered accumulator, 8 columns at a time; each piece goes
+        // through the warp's 2 KB shared-memory slice so that 8 lanes then write (or
+        // read-modify-write) one row's 64 contiguous bytes
+        const int ew = warp - 4;               // 0..15
+        const int wq = warp & 3;               // TMEM lane quarter this warp may access
+        const int qc = ew >> 2;                // column quarter
+        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+        float2 *sl = reinterpret_cast<float2 *>(sgen + OFF_OSTG + ew * (OSTG_WARP / 2));  // [32 rows][8]
+        uint32_t af_phase = 0;
+        for (long long it = 0; it < my_items; ++it) {
+            const Item itm = get_item(p, &tmap, it);
+            const int chan = itm.chan;
+            const int I0 = itm.bi * TILE, J0 = itm.bj * TILE;
+            const int i = I0 + wq * 32 + lane;  // this lane's row while staging
+            if (!tc::mbar_wait(accf_bar(0), af_phase, abort_flag, p.status)) break;
+            af_phase ^= 1u;
+            tc::tc_fence_after();
+            const uint32_t d = tmem + lane_off + (uint32_t)(32 * qc);
+            // triangle: rows i < n_in, columns j <= i of the packed accumulator (or the FP64
+            // buffer); rectangle: rows i < n_p of group P, columns j < n_q of group Q
+            const int gi0 = p.rect ? p.p0 : 0, gj0 = p.rect ? p.q0 : 0;
+            float2 gi = make_float2(1.f, 0.f);
+            if (p.gains && i < (p.rect ? p.n_p : itm.n_in)) gi = __ldg(p.gains + gi0 + i);
+#pragma unroll 1
+            for (int cb = 0; cb < 4; ++cb) {
+                // D1 = (re_I re_J | re_I im_J) in columns 0..255, D2 = (im_I re_J | im_I im_J) in 256..511
+                uint32_t a1[8], b2[8], a2[8], b1[8];
+                tc::tmem_ld8(d + 8u * cb, a1);
+                tc::tmem_ld8(d + 384u + 8u * cb, b2);
+                tc::tmem_ld8(d + 256u + 8u * cb, a2);
+                tc::tmem_ld8(d + 128u + 8u * cb, b1);
+                tc::tmem_wait_ld();
+                const int jb = J0 + 32 * qc + 8 * cb;  // columns jb .. jb + 7
+                // row `lane`, column x at element lane * 8 + ((x + lane / 2) & 7): two
+                // wavefronts per 8-byte store of one x and per 4-row read below
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    float2 v = make_float2(__uint_as_float(a1[x]) + __uint_as_float(b2[x]),
+                                           __uint_as_float(a2[x]) - __uint_as_float(b1[x]));
+                    if (p.gains) {
+                        const int jg = min(jb + x, (p.rect ? p.n_q : itm.n_in) - 1);  // clamped: unused past the end
+                        const float2 gj = __ldg(p.gains + gj0 + jg);
+                        const float2 w = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
+                        v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+                    }
+                    sl[lane * 8 + ((x + (lane >> 1)) & 7)] = v;
+                }
+                __syncwarp();
+                // offsets within the channel's block (below 2^32 entries: one channel's
+                // triangle or rectangle)
+                float2 val[8];
+                uint32_t off[8];
+                bool ok[8];
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) {
+                    const int r = rr * 4 + (lane >> 3), e = lane & 7;
+                    const int ii = I0 + wq * 32 + r, jj = jb + e;
+                    val[rr] = sl[r * 8 + ((e + (r >> 1)) & 7)];
+                    ok[rr] = p.rect ? (ii < p.n_p && jj < p.n_q) : (ii < itm.n_in && jj <= ii);
+                    off[rr] = p.rect ? (uint32_t)ii * (uint32_t)p.n_q + jj
+                                     : (uint32_t)(((unsigned long long)ii * (unsigned)(ii + 1)) >> 1) + jj;
+                }
+                __syncwarp();
+                // read-modify-writes: every read of a round in flight before its writes
+                if (p.vis64) {
+                    double2 *dst = p.vis64 + (long long)chan * itm.B;
+#pragma unroll
+                    for (int h4 = 0; h4 < 8; h4 += 4) {
+                        double2 o[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) o[q] = ok[h4 + q] ? __ldcg(dst + off[h4 + q]) : make_double2(0.0, 0.0);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (ok[h4 + q])
+                                dst[off[h4 + q]] = make_double2(o[q].x + (double)val[h4 + q].x, o[q].y + (double)val[h4 + q].y);
+                    }
+                } else {
+                    float2 *dst = p.rect ? static_cast<float2 *>(p.rect_out) + (long long)chan * p.n_p * p.n_q
+                                         : static_cast<float2 *>(itm.acc) + (long long)chan * itm.B;
+                    if (!p.store) {
+                        float2 o[8];
+#pragma unroll
+                        for (int rr = 0; rr < 8; ++rr) o[rr] = ok[rr] ? __ldcg(dst + off[rr]) : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int rr = 0; rr < 8; ++rr) val[rr] = make_float2(val[rr].x + o[rr].x, val[rr].y + o[rr].y);
+                    }
+#pragma unroll
+                    for (int rr = 0; rr < 8; ++rr)
+                        if (ok[rr]) dst[off[rr]] = val[rr];
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(acce_bar(0));
+        }
     } else if (W && warp >= 4) {
         // ------------------------------------------------------------ wide INT8 epilogue
         // 16 warps, four per TMEM lane quarter, each owning 32 columns of Re V and Im V:
@@ -552,8 +659,8 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
             if (!alive) break;
             write_sums16(R, itm, p, reinterpret_cast<unsigned char *>(sl), wq, qc, lane);
         }
-    } else if (!W && !S16 && warp >= 4) {
-        // ------------------------------------------------------------ epilogue (FP16, adjoint)
+    } else if (MODE == kAdj && warp >= 4) {
+        // ------------------------------------------------------------ epilogue (adjoint)
         const int ew = warp - 4;               // 0..7
         const int wq = warp & 3;               // TMEM lane quarter this warp may access
         const int h = ew >> 2;                 // column half: j in [64 h, 64 h + 64)
@@ -622,66 +729,6 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
                 ++ch;
                 if (p.part && i < itm.n_in)
                     p.part[((size_t)chan * p.nbj + itm.bj) * 2 * itm.n_in + (size_t)h * itm.n_in + i] = make_float2(pr, pi);
-            } else {
-                const int buf = (int)(ch & 1);
-                if (!tc::mbar_wait(accf_bar(buf), af_phase[buf], abort_flag, p.status)) break;
-                af_phase[buf] ^= 1u;
-                tc::tc_fence_after();
-                const uint32_t d = tmem + lane_off + (uint32_t)(buf * 256) + (uint32_t)(64 * h);
-                // triangle: row i, columns j <= i of the packed accumulator (or the FP64
-                // buffer); rectangle: row i of group P, columns j < n_q of group Q
-                const bool rowok = p.rect ? i < p.n_p : i < itm.n_in;
-                const int gi0 = p.rect ? p.p0 : 0, gj0 = p.rect ? p.q0 : 0;
-                float2 gi = make_float2(1.f, 0.f);
-                if (p.gains && rowok) gi = __ldg(p.gains + gi0 + i);
-                float2 *row = p.rect ? static_cast<float2 *>(p.rect_out) + ((size_t)chan * p.n_p + i) * p.n_q
-                                     : static_cast<float2 *>(itm.acc) + (size_t)chan * itm.B + (size_t)i * (i + 1) / 2;
-                const int jend = p.rect ? p.n_q - 1 : i;  // last valid column of this row
-#pragma unroll 1
-                for (int cb = 0; cb < 4; ++cb) {
-                    uint32_t re[16], im[16];
-                    tc::tmem_ld16(d + 16u * cb, re);
-                    tc::tmem_ld16(d + 128u + 16u * cb, im);
-                    tc::tmem_wait_ld();
-                    if (rowok) {
-                        const int jb = J0 + 64 * h + 16 * cb;  // columns jb .. jb + 15 of row i
-                        float2 v[16];
-#pragma unroll
-                        for (int x = 0; x < 16; ++x) {
-                            v[x] = make_float2(__uint_as_float(re[x]), __uint_as_float(im[x]));
-                            if (p.gains && jb + x <= jend) {
-                                const float2 gj = __ldg(p.gains + gj0 + jb + x);
-                                const float2 w = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
-                                v[x] = make_float2(v[x].x * w.x - v[x].y * w.y, v[x].x * w.y + v[x].y * w.x);
-                            }
-                        }
-                        // read-modify-writes: every read of the row piece in flight before any write
-                        if (p.vis64) {
-                            double2 *r64 = p.vis64 + (size_t)chan * itm.B + (size_t)i * (i + 1) / 2 + jb;
-                            double2 o[16];
-#pragma unroll
-                            for (int x = 0; x < 16; ++x) o[x] = jb + x <= i ? __ldcg(r64 + x) : make_double2(0.0, 0.0);
-#pragma unroll
-                            for (int x = 0; x < 16; ++x)
-                                if (jb + x <= i) r64[x] = make_double2(o[x].x + (double)v[x].x, o[x].y + (double)v[x].y);
-                        } else {
-                            float2 *r = row + jb;
-                            if (!p.store) {
-                                float2 o[16];
-#pragma unroll
-                                for (int x = 0; x < 16; ++x) o[x] = jb + x <= jend ? __ldcg(r + x) : make_float2(0.f, 0.f);
-#pragma unroll
-                                for (int x = 0; x < 16; ++x) v[x] = make_float2(v[x].x + o[x].x, v[x].y + o[x].y);
-                            }
-#pragma unroll
-                            for (int x = 0; x < 16; ++x)
-                                if (jb + x <= jend) r[x] = v[x];
-                        }
-                    }
-                }
-                tc::tc_fence_before();
-                tc::mbar_arrive(acce_bar(buf));
-                ++ch;
             }
         }
     }
@@ -742,6 +789,22 @@ corr_status launch_int8_wide(const CUtensorMap &tmap, const TParams &p, unsigned
     auto kern = k_xeng_tma<kInt8, C, false, true>;
     CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
     kern<<<grid, NTHREADS_WIDE, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+    return CORR_OK;
+}
+
+// FP16 and hi/lo launches (triangle, rectangle): the wide form, 640 threads.
+corr_status launch_fp16_wide(const CUtensorMap &tmap, const TParams &p, int npl, unsigned grid, cudaStream_t st) {
+    if (npl == 2) {
+        using C = TCfg<2, 64>;
+        auto kern = k_xeng_tma<kFp16, C, false, true>;
+        CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+        kern<<<grid, NTHREADS_WIDE, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+    } else {
+        using C = TCfg<4, 32>;
+        auto kern = k_xeng_tma<kFp16, C, false, true>;
+        CORR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+        kern<<<grid, NTHREADS_WIDE, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+    }
     return CORR_OK;
 }
 
@@ -817,14 +880,9 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
     } else if (h.precision == CORR_PREC_INT8) {
         const corr_status s = launch_int8_wide(tmap, p, grid, st);
         if (s != CORR_OK) return s;
-    } else if (npl == 2) {
-        using C = TCfg<2, 64>;
-        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
     } else {
-        using C = TCfg<4, 32>;
-        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+        const corr_status s = launch_fp16_wide(tmap, p, npl, grid, st);
+        if (s != CORR_OK) return s;
     }
     return check_launch("k_xeng_tma");
 }
@@ -873,14 +931,9 @@ corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl
     if (h.precision == CORR_PREC_INT8) {
         const corr_status s = launch_int8_wide(tmap, p, grid, st);
         if (s != CORR_OK) return s;
-    } else if (npl == 2) {
-        using C = TCfg<2, 64>;
-        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
     } else {
-        using C = TCfg<4, 32>;
-        CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kFp16, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-        k_xeng_tma<kFp16, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(tmap, tmap, p);
+        const corr_status s = launch_fp16_wide(tmap, p, npl, grid, st);
+        if (s != CORR_OK) return s;
     }
     return check_launch("k_xeng_tma (rectangle)");
 }
