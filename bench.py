@@ -487,6 +487,48 @@ def run_ours(args):
     return 0
 
 
+def run_short_time_only(args):
+    """Profiling mode: only the short-time INT8 X-engine (512-spectrum blocks) on the
+    chosen INT8 workload, after one F-engine pass; `warmup` untimed calls (each followed
+    by a dump), then `steps` timed calls. Every X-engine launch of the process is a
+    short-time one, so a profiler can select them by kernel name and launch count."""
+    import torch
+    from paper_1305_5639_gb300 import api
+
+    n_ant, n_pol, N, K = WORKLOADS[args.workload]
+    dev = torch.device("cuda", 0)
+    corr = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
+    g = torch.Generator(device=dev).manual_seed(0)
+    volt = torch.randint(-127, 128, (n_ant * n_pol, K * N, 2), dtype=torch.int8, device=dev, generator=g)
+    chan = corr.chan_buffer()
+    corr.fengine(volt, torch.full((N,), 1.0 / np.sqrt(N), device=dev), chan)
+    del volt
+    st = corr.set_short_time(512)
+    for _ in range(args.warmup):
+        corr.xengine(chan)
+        corr.dump(copy=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        corr.xengine(chan)
+        corr.dump(copy=False)
+    b.record()
+    torch.cuda.synchronize()
+    corr.check_status()
+    ms = a.elapsed_time(b) / args.steps
+    cmac = float(N) * (n_ant * n_pol) * (n_ant * n_pol + 1) / 2 * K
+    print(json.dumps({"metric": "short-time X-engine + dump complex-MAC/s", "value": cmac / (ms * 1e-3),
+                      "unit": "cMAC/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "int8", "data": "synthetic",
+                      "config": {"workload": f"INT8 short-time X-engine: {n_ant * n_pol} inputs, {N} channels, "
+                                             f"{K} spectra, uniform random int8 voltages through the F-engine",
+                                 "block_spectra": 512,
+                                 "block_bytes_per_call": int(st.numel() * 4)}}), flush=True)
+    corr.close()
+    return 0
+
+
 def run_batched(args):
     """Batched workload: 64 sub-arrays (antennas log-uniform 32-2048, channels from
     {256, 1024, 4096}, 512-4096 spectra, complex int8 sigma=16 as planar FP16
@@ -756,6 +798,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--short-time", action="store_true",
                     help="INT8 planar workloads: also time the X-engine writing 512-spectrum short-time visibilities")
+    ap.add_argument("--only-short-time", action="store_true",
+                    help="profiling mode: only the short-time INT8 X-engine (+ dump) on the chosen INT8 workload")
     ap.add_argument("--cross", action="store_true",
                     help="INT8 planar workloads: also time the cross-only rectangle between the two input halves")
     ap.add_argument("--pfb", type=int, default=0,
@@ -771,6 +815,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_short_time:
+        return run_short_time_only(args)
     if args.workload == "E":
         return run_batched(args)
     if args.workload == "D":
