@@ -231,6 +231,17 @@ CORR_API corr_status corr_get_accum(corr_t *h, void *out, void *stream);
  * ([n_chan][B] complex double, device). Asynchronous. */
 CORR_API corr_status corr_dump(corr_t *h, double *vis_out, void *stream);
 
+/* Checkpoint / resume of the long integration: set the handle's FP64 buffer to
+ *   vis_in [n_chan][B] complex double (device, 16-byte aligned; e.g. a buffer that
+ *          corr_dump's vis_out filled earlier, in this process or another), or to
+ *          zeros if vis_in is NULL.
+ * The integration accumulator is cleared as by corr_dump (an integration in
+ * progress is dropped), so the next X-engine call starts a new integration that
+ * corr_dump adds to the restored buffer. Asynchronous on stream; the caller keeps
+ * ownership of vis_in and may reuse it once the stream has passed this call.
+ * Misaligned vis_in: CORR_EINVAL. */
+CORR_API corr_status corr_restore_vis(corr_t *h, const double *vis_in, void *stream);
+
 /* The whole step from host memory: raw voltages in, FP64 visibilities out, with
  * the host<->device copies pipelined against the kernels on two library-owned copy
  * streams (8 input blocks: copy-in overlaps the F-engine; 8 channel blocks:
@@ -255,6 +266,16 @@ CORR_API corr_status corr_fx_host(corr_t *h, const void *volt_host, const float 
  * another CORR_* code) if a kernel of this handle gave up early since the last
  * check, CORR_OK otherwise. Synchronises `stream`. */
 CORR_API corr_status corr_check_status(corr_t *h, void *stream);
+
+/* Self-test of the failure detection every pipelined kernel relies on (its bounded
+ * device-side waits): on `device`, one thread waits on an mbarrier that nothing
+ * completes, with a time limit of limit_ns nanoseconds (1e6 .. 1e9). The wait must
+ * give up after that limit, record CORR_ETIMEOUT in a device status word and return
+ * instead of hanging; the barrier must then still complete on one arrival, and the
+ * context stays usable. Synchronous. Returns CORR_OK when all of that happened,
+ * CORR_ESTATE when the wait did not behave so, CORR_EINVAL for a limit out of range,
+ * CORR_ECUDA on a CUDA error. */
+CORR_API corr_status corr_selftest_bounded_wait(int32_t device, int64_t limit_ns);
 
 /* Zero the accumulator and the FP64 long-integration buffer. */
 CORR_API corr_status corr_reset(corr_t *h, void *stream);

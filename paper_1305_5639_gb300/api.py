@@ -99,6 +99,15 @@ def corr_dump(h, vis_out=None, stream=None) -> None:
     check(_lib.load().corr_dump(h, _ptr(vis_out), _stream(stream)), "corr_dump")
 
 
+def corr_restore_vis(h, vis_in=None, stream=None) -> None:
+    check(_lib.load().corr_restore_vis(h, _ptr(vis_in), _stream(stream)), "corr_restore_vis")
+
+
+def corr_selftest_bounded_wait(device: int = 0, limit_ns: int = 20_000_000) -> None:
+    """Run the device-side bounded-wait self-test (raises CorrError if it fails)."""
+    check(_lib.load().corr_selftest_bounded_wait(int(device), int(limit_ns)), "corr_selftest_bounded_wait")
+
+
 def corr_check_status(h, stream=None) -> None:
     check(_lib.load().corr_check_status(h, _stream(stream)), "corr_check_status")
 
@@ -232,6 +241,14 @@ class Correlator:
 
     def check_status(self, stream=None):
         corr_check_status(self.h, stream)
+
+    def restore_vis(self, vis=None, stream=None):
+        """Checkpoint / resume: set the FP64 long integration to `vis` ([n_chan, B]
+        complex128 on the device, e.g. an earlier dump()), or to zeros."""
+        if vis is not None and (vis.dtype != torch.complex128 or tuple(vis.shape) != (self.n_chan, self.n_base)
+                                or not vis.is_contiguous()):
+            raise ValueError(f"vis must be a contiguous complex128 [{self.n_chan}, {self.n_base}] tensor")
+        corr_restore_vis(self.h, vis, stream)
 
     def reset(self, stream=None):
         corr_reset(self.h, stream)

@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 namespace corr {
@@ -30,6 +32,13 @@ corr_status check_launch(const char *what) {
 }
 
 namespace {
+
+// NVTX range around a C-ABI call (visible in a profiler's timeline; a no-op when no
+// tool is attached)
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+};
 
 struct DeviceGuard {
     int prev = -1;
@@ -332,6 +341,7 @@ corr_status corr_destroy(corr_t *c) {
 }
 
 corr_status corr_fengine(corr_t *c, const void *volt, const float *chan_scale, void *chan_out, void *stream) {
+    corr::NvtxScope nvtx_("corr_fengine");
     if (!c || !volt || !chan_out) return CORR_EINVAL;
     Handle &h = c->h;
     if (!corr::fengine_supported(h.n_chan)) return CORR_EUNSUPPORTED;
@@ -346,6 +356,7 @@ corr_status corr_fengine(corr_t *c, const void *volt, const float *chan_scale, v
 }
 
 corr_status corr_fengine_power(corr_t *c, const void *volt, float *power, void *stream) {
+    corr::NvtxScope nvtx_("corr_fengine_power");
     if (!c || !volt || !power) return CORR_EINVAL;
     Handle &h = c->h;
     if (!corr::fengine_supported(h.n_chan)) return CORR_EUNSUPPORTED;
@@ -355,6 +366,7 @@ corr_status corr_fengine_power(corr_t *c, const void *volt, float *power, void *
 }
 
 corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, void *stream) {
+    corr::NvtxScope nvtx_("corr_xengine");
     if (!c || !chan_in) return CORR_EINVAL;
     Handle &h = c->h;
     if (!corr::aligned16(chan_in)) return CORR_EINVAL;
@@ -403,6 +415,7 @@ corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, voi
 
 corr_status corr_xengine_cross(corr_t *c, const void *chan_in, const float *gains, int32_t p0, int32_t n_p,
                                int32_t q0, int32_t n_q, void *vis_out, void *stream) {
+    corr::NvtxScope nvtx_("corr_xengine_cross");
     if (!c || !chan_in || !vis_out) return CORR_EINVAL;
     Handle &h = c->h;
     if (p0 < 0 || q0 < 0 || n_p <= 0 || n_q <= 0 || (int64_t)p0 + n_p > h.n_in || (int64_t)q0 + n_q > h.n_in)
@@ -436,6 +449,7 @@ corr_status corr_xengine_cross(corr_t *c, const void *chan_in, const float *gain
 }
 
 corr_status corr_get_accum(corr_t *c, void *out, void *stream) {
+    corr::NvtxScope nvtx_("corr_get_accum");
     if (!c || !out) return CORR_EINVAL;
     Handle &h = c->h;
     if (h.flags & CORR_FLAG_FUSED_DUMP) return CORR_ESTATE;
@@ -449,6 +463,7 @@ corr_status corr_get_accum(corr_t *c, void *out, void *stream) {
 }
 
 corr_status corr_dump(corr_t *c, double *vis_out, void *stream) {
+    corr::NvtxScope nvtx_("corr_dump");
     if (!c) return CORR_EINVAL;
     Handle &h = c->h;
     corr::DeviceGuard dg(h.device);
@@ -466,7 +481,32 @@ corr_status corr_dump(corr_t *c, double *vis_out, void *stream) {
     return CORR_OK;
 }
 
+corr_status corr_restore_vis(corr_t *c, const double *vis_in, void *stream) {
+    corr::NvtxScope nvtx_("corr_restore_vis");
+    if (!c) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (vis_in && !corr::aligned16(vis_in)) return CORR_EINVAL;
+    corr::DeviceGuard dg(h.device);
+    cudaStream_t st = corr::as_stream(stream);
+    const size_t bytes = (size_t)h.n_chan * h.n_base * sizeof(double2);
+    if (vis_in) CORR_CUDA_TRY(cudaMemcpyAsync(h.vis64, vis_in, bytes, cudaMemcpyDeviceToDevice, st));
+    else CORR_CUDA_TRY(cudaMemsetAsync(h.vis64, 0, bytes, st));
+    h.acc_zero = true;
+    h.acc_spectra = 0;
+    return CORR_OK;
+}
+
+corr_status corr_selftest_bounded_wait(int32_t device, int64_t limit_ns) {
+    if (limit_ns < 1000000 || limit_ns > 1000000000) return CORR_EINVAL;
+    int n_dev = 0;
+    CORR_CUDA_TRY(cudaGetDeviceCount(&n_dev));
+    if (device < 0 || device >= n_dev) return CORR_EINVAL;
+    corr::DeviceGuard dg(device);
+    return corr::selftest_bounded_wait((uint64_t)limit_ns);
+}
+
 corr_status corr_fx_host(corr_t *c, const void *volt_host, const float *chan_scale, double *vis_host, void *stream) {
+    corr::NvtxScope nvtx_("corr_fx_host");
     if (!c || !volt_host || !chan_scale || !vis_host) return CORR_EINVAL;
     Handle &h = c->h;
     if (h.precision != CORR_PREC_INT8 || !(h.flags & CORR_FLAG_PLANAR) || !corr::fengine_supported(h.n_chan))
@@ -562,6 +602,7 @@ corr_status corr_reset(corr_t *c, void *stream) {
 
 corr_status corr_backward(corr_t *c, const float *grad_vis, const void *chan_in, const float *gains, float *grad_chan,
                           float *grad_gains, void *stream) {
+    corr::NvtxScope nvtx_("corr_backward");
     if (!c || !grad_vis || !chan_in) return CORR_EINVAL;
     Handle &h = c->h;
     if (h.precision != CORR_PREC_FP32 && h.precision != CORR_PREC_FP16_HILO) return CORR_ESTATE;

@@ -94,6 +94,10 @@ corr_status launch_adj_reduce(const float2 *part, double2 *scratch, float2 *dg, 
 // [p0, p0 + n_p) x [q0, q0 + n_q), output [n_chan][n_p][n_q] overwritten.
 corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl, const float2 *gains, int p0,
                                     int n_p, int q0, int n_q, void *out, cudaStream_t st);
+// Bounded-wait self-test (selftest.cu): CORR_OK if a wait that nothing completes gave up
+// after limit_ns, recorded CORR_ETIMEOUT and returned.
+corr_status selftest_bounded_wait(uint64_t limit_ns);
+
 // Polyphase filter bank: FIR pass of inputs [i0, i0 + n_run) into h.pfb_y (pfb.cu).
 corr_status launch_pfb_fir(const Handle &h, const void *volt, int i0, int n_run, cudaStream_t st);
 bool fengine_supported(int n_chan);
