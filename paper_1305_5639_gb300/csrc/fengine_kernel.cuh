@@ -5,13 +5,17 @@
 // Each N = T x T point FFT is computed by T threads in two register passes
 // (four-step / Cooley-Tukey split n = t + T m, k = k1 + T k2):
 //   pass 1: thread t holds x[t + T m], m < T, and computes the T-point DFT over m;
-//           the result is multiplied by W_N^(t k1) (twiddle table, L1-resident)
+//           the result is multiplied by W_N^(t k1) (twiddle table copied to shared
+//           memory per CTA)
 //   exchange through shared memory (padded rows, conflict-free)
 //   pass 2: thread k1 holds Y[t][k1], t < T, and computes the T-point DFT over t,
 //           giving X[k1 + T k2].
 // A CTA handles one input and SB consecutive spectra; the outputs are staged in
 // shared memory as [channel][spectrum] so that every (channel, input) row segment
-// of SB spectra is written to global memory contiguously (the corner turn).
+// of SB spectra is written to global memory contiguously (the corner turn). Raw
+// int8 frames of the plain front end arrive by asynchronous copies into the FFT's
+// exchange buffer while the previous frame's pass 2 runs, and enter pass 1 scaled by
+// 256 on an offset that the first butterflies cancel (i8_to_f2_scaled).
 //
 // This header holds the kernel template; the per-feature translation units
 // (fengine_plain.cu, fengine_delay.cu) instantiate it, so that the instantiations
