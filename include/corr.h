@@ -212,7 +212,7 @@ CORR_API corr_status corr_set_short_time(corr_t *h, int32_t block_spectra, int32
 /* Cross-only X-engine: the rectangle of the visibility matrix between two input
  * ranges, V_ij = sum_a X_ai conj(X_aj) for i in [p0, p0 + n_p), j in [q0, q0 + n_q)
  * (Eq. 2 without the triangle restriction; two disjoint groups give the paper's
- * space-division node block, Section 3). One integration of chan_in, written to
+ * space-division node block, Section 4). One integration of chan_in, written to
  *   vis_out [n_chan][n_p][n_q]: complex int32 (2 x int32) for INT8, complex float
  *           otherwise; 8-byte aligned device memory, overwritten.
  * chan_in and gains as for corr_xengine (gains: g_i conj(g_j), float precisions).
