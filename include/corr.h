@@ -93,15 +93,19 @@ typedef struct corr_opts {
 } corr_opts;
 
 /* Create a correlator for n_ant x n_pol inputs, an n_chan-point FFT (n_chan
- * channels) and n_spectra spectra per integration (Section 2: A spectra per
- * accumulation). opts may be NULL (FP32, AUTO, current device).
+ * channels) and n_spectra spectra per integration (Section 2: the streams, the
+ * FFT length and the A spectra of one accumulation; the handle itself, its
+ * precisions and flags have no counterpart in the paper). opts may be NULL
+ * (FP32, AUTO, current device). n_ant * n_pol <= 65535 (CORR_EINVAL otherwise).
  * The F-engine supports n_chan in {16, 64, 256, 1024}; the X-engine any
- * n_chan >= 1. For INT8, n_spectra * 2 * 127^2 must stay below 2^31
- * (CORR_EOVERFLOW otherwise). *out receives the handle (NULL on error). */
+ * n_chan >= 1. For INT8, n_spectra * 2 * 128^2 must stay below 2^31
+ * (int8 codes include -128; CORR_EOVERFLOW otherwise). *out receives the handle
+ * (NULL on error). */
 CORR_API corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_spectra,
                         const corr_opts *opts, corr_t **out);
 
-/* Free every library-owned buffer. Synchronises the device. NULL is accepted. */
+/* Free every library-owned buffer (no counterpart in the paper). Synchronises the
+ * device. NULL is accepted. */
 CORR_API corr_status corr_destroy(corr_t *h);
 
 /* Static string for a status code. */
@@ -172,12 +176,15 @@ CORR_API corr_status corr_fengine_power(corr_t *h, const void *volt, float *powe
  *   power     [n_chan] float, device: sum_{i,a} |S_a,i[k]|^2 / (2 n_in n_spectra).
  * n_chan must be one of 16, 64, 256, 1024: larger values are rejected with
  * CORR_EINVAL (the static scratch holds 1024 FP64 accumulators), others with
- * CORR_EUNSUPPORTED. The scratch and twiddle tables are file-scope device arrays
- * (about 19 KB) that each GPU loading the library keeps until the process exits.
- * The first call on a device sets them up (a synchronous host-to-device copy)
- * and should be made before any stream capture. All calls on a device share the
- * scratch: calls that overlap on the GPU race, so serialise them (one stream,
- * or events). Runs on the current device and `stream`. */
+ * CORR_EUNSUPPORTED; n_in must be at most 65535 (CORR_EINVAL). Every rejection
+ * sets corr_last_error(). The scratch and the (compile-time) twiddle tables are
+ * file-scope device arrays (about 19 KB) that each GPU loading the library keeps
+ * until the process exits. Each call looks up their device addresses in the
+ * current context (no allocation); the first call on a device may load the
+ * library's device code, so make it before any stream capture. All calls on a
+ * device share the scratch and clear it first: calls that overlap on the GPU race,
+ * so serialise them (one stream, or events). Runs on the current device and
+ * `stream`. */
 CORR_API corr_status corr_fengine_power_noalloc(const void *volt, int32_t n_in, int32_t n_chan,
                                                 int32_t n_spectra, int32_t precision, float *power,
                                                 void *stream);
@@ -228,7 +235,9 @@ CORR_API corr_status corr_get_accum(corr_t *h, void *out, void *stream);
 
 /* Integration dump: vis64 += accumulator (FP64), accumulator = 0. If vis_out is
  * not NULL, the FP64 long-integration buffer is copied to it
- * ([n_chan][B] complex double, device). Asynchronous. */
+ * ([n_chan][B] complex double, device). Asynchronous. The paper writes each
+ * accumulation's visibilities out (Section 5, Section 6.3); the FP64 long
+ * integration is this library's own addition, with no passage behind it. */
 CORR_API corr_status corr_dump(corr_t *h, double *vis_out, void *stream);
 
 /* Checkpoint / resume of the long integration: set the handle's FP64 buffer to
@@ -280,7 +289,9 @@ CORR_API corr_status corr_selftest_bounded_wait(int32_t device, int64_t limit_ns
 /* Zero the accumulator and the FP64 long-integration buffer. */
 CORR_API corr_status corr_reset(corr_t *h, void *stream);
 
-/* Adjoint of corr_xengine (with gains) for gradient-based gain calibration.
+/* Adjoint of corr_xengine (with gains) for gradient-based gain calibration. The
+ * paper has no adjoint: this is the derivative of Eq. 2 with per-input gains
+ * applied, for a loss over the visibilities, derived for this library.
  *   grad_vis  [n_chan][B] complex float: G_ij = dL/dV'_ij (PyTorch convention
  *             dL/dRe + j dL/dIm) of the gained visibilities, packed i >= j.
  *   chan_in   [n_chan][n_in][n_spectra] complex float: the forward input X.
@@ -314,22 +325,29 @@ typedef struct corr_batch_s corr_batch_t;
 typedef struct corr_sub_desc {
     int32_t n_in;       /* inputs of the sub-array (1..65535) */
     int32_t n_chan;     /* channels */
-    int32_t n_spectra;  /* spectra per integration: a multiple of 8, with n_spectra * 2 * 127^2 < 2^31 */
+    int32_t n_spectra;  /* spectra per integration: a multiple of 8, with n_spectra * 2 * 128^2 < 2^31 */
     int32_t reserved;   /* must be 0 */
     const void *planes; /* device, [n_chan][2][n_in][n_spectra] FP16 codes, 16-byte aligned */
     int32_t *vis;       /* device, [n_chan][n_in (n_in + 1) / 2][2] INT32, 8-byte aligned */
 } corr_sub_desc;
 
-/* Plan a batch on the current device: every (sub-array, channel, lower-triangle
- * tile) work item is spread over one CTA per SM, longest first. The descriptor
- * array is copied; the device buffers it names must outlive the batch. */
-CORR_API corr_status corr_batch_create(int32_t n_sub, const corr_sub_desc *subs, corr_batch_t **out);
+/* Plan a batch: every (sub-array, channel, lower-triangle tile) work item is
+ * spread over one CTA per SM, longest first. The descriptor array is copied; the
+ * device buffers it names must outlive the batch.
+ *   opts  NULL (INT8, current device) or precision CORR_PREC_INT8, xengine AUTO or
+ *         TCGEN05, flags 0 or CORR_FLAG_PLANAR (the inputs are planar codes either
+ *         way) and the device ordinal (-1: current); anything else is
+ *         CORR_EUNSUPPORTED. Every later call on the batch runs on that device.
+ * INT32 guard: each sub-array needs n_spectra * 2 * 128^2 < 2^31 (CORR_EOVERFLOW). */
+CORR_API corr_status corr_batch_create(int32_t n_sub, const corr_sub_desc *subs, const corr_opts *opts,
+                                       corr_batch_t **out);
 
 /* Choose each sub-array's tile shape by timing: sub-arrays of <= 64 (<= 32)
  * inputs may pack 2 (up to 4) channels into one 128-row tensor-core tile. The
  * choices are read from / written to the JSON file cache_path (NULL: no cache)
- * keyed by (inputs, spectra), and the batch is re-planned. Synchronises stream;
- * runs the sub-arrays (overwriting their outputs) while timing. */
+ * keyed by (inputs, spectra), and the batch is re-planned. The timing runs are
+ * queued on `stream` (so that they are ordered after the caller's writes of the
+ * inputs), which this call synchronises; they overwrite the sub-arrays' outputs. */
 CORR_API corr_status corr_batch_tune(corr_batch_t *b, const char *cache_path, void *stream);
 
 /* Correlate every sub-array: one graph launch on `stream` (the graph is captured

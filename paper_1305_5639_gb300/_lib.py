@@ -63,7 +63,8 @@ SIGNATURES = [
     ("corr_fengine_power_noalloc", _S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         _P, _P]),
     ("corr_fx_host", _S, [_P, _P, _P, _P, _P]),
-    ("corr_batch_create", _S, [ctypes.c_int32, ctypes.POINTER(corr_sub_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    ("corr_batch_create", _S, [ctypes.c_int32, ctypes.POINTER(corr_sub_desc), ctypes.POINTER(corr_opts),
+                               ctypes.POINTER(ctypes.c_void_p)]),
     ("corr_batch_tune", _S, [_P, ctypes.c_char_p, _P]),
     ("corr_batch_run", _S, [_P, _P]),
     ("corr_batch_check_status", _S, [_P, _P]),

@@ -260,13 +260,14 @@ class Correlator:
         return gc, gg
 
 
-def corr_batch_create(subs) -> ctypes.c_void_p:
+def corr_batch_create(subs, device: int = -1) -> ctypes.c_void_p:
     """subs: sequence of (planes, n_in, n_chan, n_spectra, vis) with device tensors."""
     arr = (_lib.corr_sub_desc * len(subs))()
     for k, (planes, n_in, n_chan, K, vis) in enumerate(subs):
         arr[k] = _lib.corr_sub_desc(int(n_in), int(n_chan), int(K), 0, _ptr(planes), _ptr(vis))
+    o = corr_opts(PREC["int8"], XENG["auto"], _lib.CORR_FLAG_PLANAR, int(device))
     b = ctypes.c_void_p()
-    check(_lib.load().corr_batch_create(len(subs), arr, ctypes.byref(b)), "corr_batch_create")
+    check(_lib.load().corr_batch_create(len(subs), arr, ctypes.byref(o), ctypes.byref(b)), "corr_batch_create")
     return b
 
 
@@ -305,7 +306,8 @@ class Batch:
             v = torch.zeros((n_chan, n_in * (n_in + 1) // 2, 2), dtype=torch.int32, device=p.device)
             self.vis.append(v)
             subs.append((p, n_in, n_chan, K, v))
-        self.b = corr_batch_create(subs)
+        dev = self.planes[0].device.index if self.planes else -1
+        self.b = corr_batch_create(subs, -1 if dev is None else dev)
 
     def tune(self, cache_path=None, stream=None):
         corr_batch_tune(self.b, cache_path, stream)

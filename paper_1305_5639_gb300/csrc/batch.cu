@@ -206,10 +206,21 @@ using corr::Plan;
 
 extern "C" {
 
-corr_status corr_batch_create(int32_t n_sub, const corr_sub_desc *subs, corr_batch_t **out) {
+corr_status corr_batch_create(int32_t n_sub, const corr_sub_desc *subs, const corr_opts *opts, corr_batch_t **out) {
     if (!out) return CORR_EINVAL;
     *out = nullptr;
     if (n_sub <= 0 || !subs) return CORR_EINVAL;
+    // the batched X-engine is the exact INT8 one on tensor cores, fed planar FP16 codes
+    int device = -1;
+    if (opts) {
+        if (opts->precision != CORR_PREC_INT8 || opts->xengine == CORR_XENG_CUDACORE ||
+            (opts->flags & ~CORR_FLAG_PLANAR) != 0) {
+            corr::set_error_text("corr_batch_create: only INT8 on the tensor-core X-engine (planar codes) is batched");
+            return CORR_EUNSUPPORTED;
+        }
+        if (opts->xengine < CORR_XENG_AUTO || opts->xengine > CORR_XENG_TCGEN05) return CORR_EINVAL;
+        device = opts->device;
+    }
     for (int s = 0; s < n_sub; ++s) {
         const corr_sub_desc &d = subs[s];
         if (d.n_in <= 0 || d.n_in > 65535 || d.n_chan <= 0 || d.n_spectra <= 0 || d.reserved != 0 || !d.planes || !d.vis)
@@ -217,13 +228,24 @@ corr_status corr_batch_create(int32_t n_sub, const corr_sub_desc *subs, corr_bat
         if ((reinterpret_cast<uintptr_t>(d.planes) & 15u) || (reinterpret_cast<uintptr_t>(d.vis) & 7u))
             return CORR_EINVAL;
         if (d.n_spectra % 8 != 0) return CORR_EUNSUPPORTED;
-        if ((int64_t)d.n_spectra * 2 * 127 * 127 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
+        // INT32 guard: |V| <= n_spectra * 2 * 128^2 (int8 codes include -128)
+        if ((int64_t)d.n_spectra * 2 * 128 * 128 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
+    }
+    if (device < 0 && cudaGetDevice(&device) != cudaSuccess) {
+        corr::set_cuda_error(cudaGetLastError(), "cudaGetDevice");
+        return CORR_ECUDA;
+    }
+    corr::DeviceGuard dg(device);
+    if (!dg.ok) {
+        corr::set_cuda_error(cudaGetLastError(), "cudaSetDevice");
+        return CORR_ECUDA;
     }
     corr_batch_s *b = new (std::nothrow) corr_batch_s();
     if (!b) return CORR_ENOMEM;
     b->subs.assign(subs, subs + n_sub);
     b->cpt.assign((size_t)n_sub, 1);
-    bool ok = cudaGetDevice(&b->device) == cudaSuccess &&
+    b->device = device;
+    bool ok = 
               cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess &&
               cudaMalloc(&b->d_tmaps, 128 * (size_t)n_sub) == cudaSuccess &&
               cudaMalloc(&b->d_subs, sizeof(corr::BatchSub) * (size_t)n_sub) == cudaSuccess &&
@@ -242,6 +264,7 @@ corr_status corr_batch_create(int32_t n_sub, const corr_sub_desc *subs, corr_bat
 
 corr_status corr_batch_destroy(corr_batch_t *b) {
     if (!b) return CORR_OK;
+    corr::DeviceGuard dg(b->device);
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -261,6 +284,7 @@ int32_t corr_batch_channels_per_tile(const corr_batch_t *b, int32_t sub) {
 
 corr_status corr_batch_run(corr_batch_t *b, void *stream) {
     if (!b) return CORR_EINVAL;
+    corr::DeviceGuard dg(b->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!b->exec) {
         // capture the single persistent launch on a private stream, then replay it
@@ -291,6 +315,7 @@ corr_status corr_batch_run(corr_batch_t *b, void *stream) {
 
 corr_status corr_batch_check_status(corr_batch_t *b, void *stream) {
     if (!b) return CORR_EINVAL;
+    corr::DeviceGuard dg(b->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int v = 0;
     CORR_CUDA_TRY(cudaMemcpyAsync(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -304,6 +329,7 @@ corr_status corr_batch_check_status(corr_batch_t *b, void *stream) {
 
 corr_status corr_batch_tune(corr_batch_t *b, const char *cache_path, void *stream) {
     if (!b) return CORR_EINVAL;
+    corr::DeviceGuard dg(b->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::map<std::string, int> cache = corr::read_cache(cache_path);
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -40,21 +40,24 @@ struct NvtxScope {
     ~NvtxScope() { nvtxRangePop(); }
 };
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 inline cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+// Host-buffer pipeline resources (corr_fx_host): device copies, copy streams, events.
+void free_fx(Handle &h) {
+    cudaFree(h.fx_volt);
+    cudaFree(h.fx_chan);
+    h.fx_volt = h.fx_chan = nullptr;
+    if (h.fx_in) cudaStreamDestroy(h.fx_in);
+    if (h.fx_out) cudaStreamDestroy(h.fx_out);
+    h.fx_in = h.fx_out = nullptr;
+    for (cudaEvent_t &e : h.fx_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    h.fx_ready = false;
+}
 
 void free_buffers(Handle &h) {
     cudaFree(h.acc);
@@ -73,16 +76,7 @@ void free_buffers(Handle &h) {
     cudaFree(h.bwd_ws);
     cudaFree(h.planar_ws);
     h.planar_ws = nullptr;
-    cudaFree(h.fx_volt);
-    cudaFree(h.fx_chan);
-    h.fx_volt = h.fx_chan = nullptr;
-    if (h.fx_in) cudaStreamDestroy(h.fx_in);
-    if (h.fx_out) cudaStreamDestroy(h.fx_out);
-    h.fx_in = h.fx_out = nullptr;
-    for (cudaEvent_t &e : h.fx_ev) {
-        if (e) cudaEventDestroy(e);
-        e = nullptr;
-    }
+    free_fx(h);
     if (h.bwd_side) cudaStreamDestroy(h.bwd_side);
     h.bwd_side = nullptr;
     for (cudaEvent_t &e : h.bwd_ev) {
@@ -138,7 +132,11 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
     *out = nullptr;
     if (n_ant <= 0 || n_pol <= 0 || n_chan <= 0 || n_spectra <= 0) return CORR_EINVAL;
     const int64_t n_in = (int64_t)n_ant * n_pol;
-    if (n_in > (1 << 16)) return CORR_EINVAL;
+    if (n_in > 65535) {
+        // the F-engine's grid holds one input per block row (at most 65535)
+        corr::set_error_text("corr_create: n_ant * n_pol exceeds 65535 inputs");
+        return CORR_EINVAL;
+    }
     corr_opts o{CORR_PREC_FP32, CORR_XENG_AUTO, 0, -1};
     if (opts) o = *opts;
     if (o.precision < CORR_PREC_FP32 || o.precision > CORR_PREC_FP16_HILO) return CORR_EINVAL;
@@ -153,8 +151,8 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
         (o.precision != CORR_PREC_INT8 || o.xengine == CORR_XENG_CUDACORE || (n_spectra % 8) != 0))
         return CORR_EUNSUPPORTED;
     if (o.precision == CORR_PREC_INT8) {
-        // INT32 guard: |Re V| <= n_spectra * 2 * 127^2 must stay below 2^31
-        if ((int64_t)n_spectra * 2 * 127 * 127 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
+        // INT32 guard: |Re V| <= n_spectra * 2 * 128^2 (int8 codes include -128) must stay below 2^31
+        if ((int64_t)n_spectra * 2 * 128 * 128 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
     }
     if ((o.precision == CORR_PREC_FP16 || o.precision == CORR_PREC_FP16_HILO) && o.xengine == CORR_XENG_CUDACORE)
         return CORR_EUNSUPPORTED;
@@ -373,7 +371,7 @@ corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, voi
     if (gains && h.precision == CORR_PREC_INT8) return CORR_EINVAL;
     if (h.precision == CORR_PREC_INT8 && !(h.flags & CORR_FLAG_FUSED_DUMP)) {
         // the INT32 accumulator spans every call since the last dump
-        if ((h.acc_spectra + h.n_spectra) * 2 * 127 * 127 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
+        if ((h.acc_spectra + h.n_spectra) * 2 * 128 * 128 >= (int64_t)1 << 31) return CORR_EOVERFLOW;
     }
     corr::DeviceGuard dg(h.device);
     const bool store = h.acc_zero;
@@ -516,7 +514,9 @@ corr_status corr_fx_host(corr_t *c, const void *volt_host, const float *chan_sca
     constexpr int NB = 8, NC = 8;  // input blocks (copy-in || F-engine), channel blocks (X + dump || copy-out)
     const size_t volt_bytes = (size_t)h.n_in * h.n_spectra * h.n_chan * 2;
     const size_t chan_bytes = (size_t)h.n_chan * 2 * h.n_in * h.n_spectra * 2;
-    if (!h.fx_volt) {
+    if (!h.fx_ready) {
+        // all or nothing: a failed allocation or creation releases whatever this
+        // attempt made, so that a retry starts again from scratch
         bool ok = cudaMalloc(&h.fx_volt, volt_bytes) == cudaSuccess && cudaMalloc(&h.fx_chan, chan_bytes) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h.fx_in, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h.fx_out, cudaStreamNonBlocking) == cudaSuccess;
@@ -524,8 +524,11 @@ corr_status corr_fx_host(corr_t *c, const void *volt_host, const float *chan_sca
             ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
+            corr::free_fx(h);
+            corr::set_error_text("corr_fx_host: allocating the device copies or creating the copy streams failed");
             return CORR_ENOMEM;
         }
+        h.fx_ready = true;
     }
     // ev[1..NB]: input block b copied; ev[NB+1..NB+NC]: channel block dumped;
     // ev[NB+NC+1]: all copies out done; ev[NB+NC+2]: the F-engine has read the device
@@ -624,13 +627,22 @@ corr_status corr_backward(corr_t *c, const float *grad_vis, const void *chan_in,
             h.bwd_ws_bytes = need;
         }
         if (!h.bwd_side) {
-            bool ok = cudaStreamCreateWithFlags(&h.bwd_side, cudaStreamNonBlocking) == cudaSuccess;
+            cudaStream_t side = nullptr;
+            bool ok = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) == cudaSuccess;
             for (cudaEvent_t &e : h.bwd_ev)
                 ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
             if (!ok) {
+                // all or nothing, so that a retry creates everything again
                 cudaGetLastError();
+                if (side) cudaStreamDestroy(side);
+                for (cudaEvent_t &e : h.bwd_ev) {
+                    if (e) cudaEventDestroy(e);
+                    e = nullptr;
+                }
+                corr::set_error_text("corr_backward: creating the side stream or its events failed");
                 return CORR_ECUDA;
             }
+            h.bwd_side = side;
         }
         return corr::launch_backward_tc(h, reinterpret_cast<const float2 *>(grad_vis),
                                         static_cast<const float2 *>(chan_in), reinterpret_cast<const float2 *>(gains),

@@ -2,8 +2,7 @@
 // power pass and the allocation-free power pass. The kernel is in fengine_kernel.cuh.
 #include <cmath>
 #include <cstdio>
-#include <mutex>
-#include <vector>
+#include <initializer_list>
 
 #include "fengine_kernel.cuh"
 
@@ -90,66 +89,49 @@ corr_status launch_fengine_power(const Handle &h, const void *volt, float *power
 // corr_fengine_power without a handle and without allocating device memory. Its
 // scratch (the FP64 per-channel accumulators) and its twiddle tables live in
 // file-scope __device__ arrays that every GPU loading this library holds until
-// the process exits. Host code only sees a host-side stand-in for those arrays,
-// so their device addresses are fetched once per device with
-// cudaGetSymbolAddress and passed to the kernels.
+// the process exits. The twiddle tables are constant-initialised (computed at
+// compile time), so they are in place whenever the module is loaded, in any
+// context. Host code only sees a host-side stand-in for those arrays, so each
+// call looks their device addresses up with cudaGetSymbolAddress (which allocates
+// nothing) and passes them to the kernels.
 namespace {
 
 constexpr int kNaMaxChan = 1024;  // largest n_chan the static scratch holds (8 KB of FP64)
 constexpr int kNaTwTotal = 16 + 64 + 256 + 1024;
-constexpr int kNaMaxDevices = 64;
+
+constexpr int na_tw_offset(int n) {
+    return n == 16 ? 0 : n == 64 ? 16 : n == 256 ? 80 : n == 1024 ? 336 : -1;
+}
+
+// F-engine twiddle tables W_N^(t k1) = exp(-j 2 pi t k1 / N), [k1][t] layout with
+// N = T x T, for N = 16, 64, 256 and 1024, as (re, im) float pairs.
+struct NaTwiddles {
+    float v[2 * kNaTwTotal];
+};
+
+constexpr NaTwiddles na_make_twiddles() {
+    NaTwiddles r{};
+    for (int n : {16, 64, 256, 1024}) {
+        int T = 1;
+        while (T * T < n) T *= 2;
+        const int o = na_tw_offset(n);
+        for (int k1 = 0; k1 < T; ++k1)
+            for (int t = 0; t < T; ++t) {
+                const int j = (t * k1) % n;
+                r.v[2 * (o + k1 * T + t)] = (float)cos2pi(j, n);
+                r.v[2 * (o + k1 * T + t) + 1] = (float)-sin2pi(j, n);
+            }
+    }
+    return r;
+}
 
 // FP64 power accumulators, shared by every call on a device (cleared per call).
 static __device__ __align__(256) double g_na_power[kNaMaxChan];
-// F-engine twiddle tables, [k1][t] layout, for n_chan = 16, 64, 256 and 1024.
-static __device__ __align__(256) float2 g_na_tw[kNaTwTotal];
+static __device__ __align__(256) NaTwiddles g_na_tw = na_make_twiddles();
 
-struct NaDevice {
-    bool ready = false;
-    double *power = nullptr;
-    float2 *tw = nullptr;
-};
-NaDevice g_na_dev[kNaMaxDevices];
-std::mutex g_na_mu;
-
-int na_tw_offset(int n) {
-    switch (n) {
-        case 16: return 0;
-        case 64: return 16;
-        case 256: return 80;
-        case 1024: return 336;
-        default: return -1;
-    }
-}
-
-// Once per device, with that device current: device addresses of the static
-// arrays, and the twiddle tables (a synchronous copy, no allocation).
-corr_status na_setup(int dev, NaDevice *&out) {
-    std::lock_guard<std::mutex> lock(g_na_mu);
-    NaDevice &d = g_na_dev[dev];
-    if (!d.ready) {
-        double *pw = nullptr;
-        float2 *tw = nullptr;
-        CORR_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void **>(&pw), g_na_power));
-        CORR_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void **>(&tw), g_na_tw));
-        std::vector<float2> host(kNaTwTotal);
-        for (int n : {16, 64, 256, 1024}) {
-            int T = 1;
-            while (T * T < n) T *= 2;
-            float2 *tab = host.data() + na_tw_offset(n);
-            for (int k1 = 0; k1 < T; ++k1)
-                for (int t = 0; t < T; ++t) {
-                    const double ang = 2.0 * M_PI * (double)((t * k1) % n) / (double)n;
-                    tab[k1 * T + t] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
-                }
-        }
-        CORR_CUDA_TRY(cudaMemcpyToSymbol(g_na_tw, host.data(), sizeof(float2) * kNaTwTotal));
-        d.power = pw;
-        d.tw = tw;
-        d.ready = true;
-    }
-    out = &d;
-    return CORR_OK;
+corr_status na_reject(const char *why) {
+    set_error_text(why);
+    return CORR_EINVAL;
 }
 
 }  // namespace
@@ -158,20 +140,27 @@ corr_status na_setup(int dev, NaDevice *&out) {
 extern "C" corr_status corr_fengine_power_noalloc(const void *volt, int32_t n_in, int32_t n_chan,
                                                    int32_t n_spectra, int32_t precision, float *power,
                                                    void *stream) {
-    if (!volt || !power || n_in <= 0 || n_chan <= 0 || n_spectra <= 0) return CORR_EINVAL;
-    if (n_chan > corr::kNaMaxChan) {
-        corr::set_error_text("corr_fengine_power_noalloc: n_chan exceeds the 1024-channel static scratch");
-        return CORR_EINVAL;
+    using corr::na_reject;
+    if (!volt || !power) return na_reject("corr_fengine_power_noalloc: null volt or power");
+    if (n_in <= 0 || n_chan <= 0 || n_spectra <= 0)
+        return na_reject("corr_fengine_power_noalloc: n_in, n_chan and n_spectra must be positive");
+    if (n_in > 65535) return na_reject("corr_fengine_power_noalloc: n_in exceeds 65535 inputs");
+    if (n_chan > corr::kNaMaxChan)
+        return na_reject("corr_fengine_power_noalloc: n_chan exceeds the 1024-channel static scratch");
+    if (corr::na_tw_offset(n_chan) < 0) {
+        corr::set_error_text("corr_fengine_power_noalloc: n_chan must be 16, 64, 256 or 1024");
+        return CORR_EUNSUPPORTED;
     }
-    if (!corr::fengine_supported(n_chan)) return CORR_EUNSUPPORTED;
-    if (precision != CORR_PREC_INT8 && precision != CORR_PREC_FP32) return CORR_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(volt) & 15u) != 0) return CORR_EINVAL;
-    int dev = 0;
-    CORR_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= corr::kNaMaxDevices) return CORR_EUNSUPPORTED;
-    corr::NaDevice *d = nullptr;
-    corr_status s = corr::na_setup(dev, d);
-    if (s != CORR_OK) return s;
-    const corr::FShape f{n_in, n_chan, n_spectra, precision == CORR_PREC_INT8, d->tw + corr::na_tw_offset(n_chan)};
-    return corr::power_pass(f, volt, d->power, power, static_cast<cudaStream_t>(stream));
+    if (precision != CORR_PREC_INT8 && precision != CORR_PREC_FP32)
+        return na_reject("corr_fengine_power_noalloc: precision must be CORR_PREC_INT8 or CORR_PREC_FP32");
+    if ((reinterpret_cast<uintptr_t>(volt) & 15u) != 0)
+        return na_reject("corr_fengine_power_noalloc: volt must be 16-byte aligned");
+    // device addresses of the static arrays in the current context (no allocation)
+    double *pw = nullptr;
+    corr::NaTwiddles *tw = nullptr;
+    CORR_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void **>(&pw), corr::g_na_power));
+    CORR_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void **>(&tw), corr::g_na_tw));
+    const corr::FShape f{n_in, n_chan, n_spectra, precision == CORR_PREC_INT8,
+                         reinterpret_cast<const float2 *>(tw) + corr::na_tw_offset(n_chan)};  // v at offset 0
+    return corr::power_pass(f, volt, pw, power, static_cast<cudaStream_t>(stream));
 }

@@ -40,6 +40,7 @@ struct Handle {
     void *fx_volt = nullptr, *fx_chan = nullptr;
     cudaStream_t fx_in = nullptr, fx_out = nullptr;
     cudaEvent_t fx_ev[40] = {};
+    bool fx_ready = false;  // every fx_* resource above was created
     size_t bwd_ws_bytes = 0;
 };
 
@@ -56,6 +57,21 @@ corr_status check_launch(const char *what);
             return CORR_ECUDA;                               \
         }                                                    \
     } while (0)
+
+// Makes a device current for the lifetime of the guard and restores the previous one.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
 
 // Kernel launchers (return CORR_OK or an error status).
 corr_status launch_fengine(const Handle &h, const void *volt, const float *scale, void *out,

@@ -9,8 +9,10 @@
 //   INT8:  complex int8 input, exact INT32 result with dp4a: a 32-bit word holds
 //          (re, im) of two consecutive spectra, so
 //            Re V_ij += dp4a([re_i im_i ...], [re_j im_j ...])
-//            Im V_ij += dp4a([im_i -re_i ...], [re_j im_j ...]).
-//          Symmetric int8 clipping (+-127) keeps -re representable.
+//            Im V_ij += dp4a([im_i ~re_i ...], [re_j im_j ...]) + sum(im_j)
+//          with ~re = -re - 1 (bitwise not), representable for every int8 code
+//          including -128 (whose negation is not): the -1 terms sum to -sum(im_j),
+//          which a per-column dp4a with [0 1 0 1] adds back.
 #include "internal.h"
 
 namespace corr {
@@ -105,12 +107,12 @@ __global__ void __launch_bounds__(NTH) k_xeng_f32(const float2 *__restrict__ X, 
 }
 
 __device__ __forceinline__ uint32_t rot_word(uint32_t w) {
-    // bytes [re0 im0 re1 im1] -> [im0 -re0 im1 -re1]
-    int re0 = (int)(int8_t)(w & 0xff), im0 = (int)(int8_t)((w >> 8) & 0xff);
-    int re1 = (int)(int8_t)((w >> 16) & 0xff), im1 = (int)(int8_t)(w >> 24);
-    return (uint32_t)(im0 & 0xff) | ((uint32_t)((-re0) & 0xff) << 8) | ((uint32_t)(im1 & 0xff) << 16) |
-           ((uint32_t)((-re1) & 0xff) << 24);
+    // bytes [re0 im0 re1 im1] -> [im0 ~re0 im1 ~re1] (~re = -re - 1)
+    const uint32_t sw = __byte_perm(w, 0u, 0x2301);  // [im0 re0 im1 re1]
+    return sw ^ 0xff00ff00u;
 }
+// dp4a weights picking the imaginary bytes of a word: [0 1 0 1]
+constexpr int kImOnes = 0x01000100;
 
 __global__ void __launch_bounds__(NTH) k_xeng_i8(const char2 *__restrict__ X, int2 *__restrict__ acc,
                                                  int n_in, int K, long long B, int store) {
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(NTH) k_xeng_i8(const char2 *__restrict__ X, in
     const char2 *Xc = X + (size_t)chan * n_in * K;
 
     int ar[4][4], ai[4][4];
+    int cim[4] = {0, 0, 0, 0};  // sum of Im x_j over the spectra, per column
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -166,7 +169,10 @@ __global__ void __launch_bounds__(NTH) k_xeng_i8(const char2 *__restrict__ X, in
                 xr[r] = (int)sr[w][ty + 16 * r];
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) xj[c] = (int)sj[w][tx + 16 * c];
+            for (int c = 0; c < 4; ++c) {
+                xj[c] = (int)sj[w][tx + 16 * c];
+                cim[c] = __dp4a(xj[c], kImOnes, cim[c]);
+            }
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -185,11 +191,12 @@ __global__ void __launch_bounds__(NTH) k_xeng_i8(const char2 *__restrict__ X, in
             int j = J0 + tx + 16 * c;
             if (i < n_in && j <= i) {
                 size_t b = (size_t)chan * B + (size_t)i * (i + 1) / 2 + j;
+                const int im = ai[r][c] + cim[c];
                 if (store) {
-                    acc[b] = make_int2(ar[r][c], ai[r][c]);
+                    acc[b] = make_int2(ar[r][c], im);
                 } else {
                     int2 o = acc[b];
-                    acc[b] = make_int2(o.x + ar[r][c], o.y + ai[r][c]);
+                    acc[b] = make_int2(o.x + ar[r][c], o.y + im);
                 }
             }
         }

@@ -10,9 +10,10 @@
 // planes are stored [im | re | -im] so both B operands are contiguous 256-row
 // slices. Diagonal tiles (I == J) reuse the J planes as A.
 //
-// INT8: int8 values are exact in FP16 and every product (<= 127^2) is exact in
-// FP32; one accumulator column sums at most 2 * 127^2 * 512 < 2^24 over 512
-// spectra, so FP32 partial sums of <= 512 spectra are exact integers. After each
+// INT8: int8 values (-128 included; its negation 128 too) are exact in FP16 and
+// every product (<= 128^2) is exact in FP32; one accumulator column sums at most
+// 2 * 128^2 * 512 = 2^24 in magnitude over 512 spectra, so FP32 partial sums of
+// <= 512 spectra are exact integers. After each
 // 512-spectrum chunk the epilogue adds the FP32 partial (converted exactly) into
 // an INT32 running sum held in TMEM columns 256..511: the result is bit-exact.
 // FP16: inputs rounded to FP16, FP32 accumulation over the whole integration, with

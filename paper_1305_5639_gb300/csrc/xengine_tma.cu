@@ -9,9 +9,10 @@
 // the minus sign coming from the instruction descriptor's negate-A bit, so only
 // the Re and Im planes are stored. Diagonal tiles (I == J) load the J planes once.
 //
-// INT8 codes (|x| <= 127) are exact in FP16 and their products exact in FP32;
-// each accumulator column sums at most 2 * 127^2 * 512 < 2^24, so an FP32
-// partial over <= 512 spectra is an exact integer. The accumulator is double
+// INT8 codes (-128 <= x <= 127) are exact in FP16 and their products exact in
+// FP32; each accumulator column sums at most 2 * 128^2 * 512 = 2^24 in magnitude,
+// and every integer of magnitude <= 2^24 is an FP32 value, so an FP32 partial
+// over <= 512 spectra is an exact integer. The accumulator is double
 // buffered in TMEM (2 x 256 columns): while the MMAs fill one buffer with the next
 // 512 spectra, the epilogue converts the other exactly and adds it into INT32
 // running sums held in registers. The result is bit-exact.
@@ -266,8 +267,8 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
     // D2 += Im_I [Re_J; Im_J]^T (the J stage's two planes form one 256-row operand), so
     // each operand tile is read from shared memory once per MMA pair instead of twice;
     // the epilogue forms Re V = D1a + D2b and Im V = D2a - D1b in INT32. Each half of D1,
-    // D2 sums one kind of product, |.| <= 127^2 per spectrum, so 1024-spectrum FP32 chunks
-    // stay exact; D1 and D2 fill TMEM, so the accumulator is single-buffered.
+    // D2 sums one kind of product, |.| <= 128^2 per spectrum, so 1024-spectrum FP32 chunks
+    // (|sum| <= 2^24) stay exact; D1 and D2 fill TMEM, so the accumulator is single-buffered.
     constexpr bool W = WIDE && ((MODE == kInt8 && NPL == 2) || MODE == kFp16) && !ST;
     // short-time INT8: the narrow, double-buffered accumulator drained by 16 epilogue
     // warps (warps 4..19), each owning 32 columns of Re V and Im V for 32 rows

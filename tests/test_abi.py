@@ -68,9 +68,13 @@ def test_create_rejects_bad_arguments_without_device(lib):
     assert lib.corr_create(4, 1, 16, 12, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
     o = corr_opts(1, 0, 2, -1)  # the fused dump needs the planar X-engine
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
-    # INT8 guard: n_spectra * 2 * 127^2 must stay below 2^31 (66573 spectra is the first to fail)
+    # INT8 guard: n_spectra * 2 * 128^2 must stay below 2^31 (int8 codes include -128;
+    # 65536 spectra is the first to fail)
     o = corr_opts(1, 0, 0, -1)
-    assert lib.corr_create(4, 1, 16, 66573, ctypes.byref(o), ctypes.byref(h)) == CORR_EOVERFLOW
+    assert lib.corr_create(4, 1, 16, 65536, ctypes.byref(o), ctypes.byref(h)) == CORR_EOVERFLOW
+    # at most 65535 inputs (one F-engine grid row per input)
+    assert lib.corr_create(65536, 1, 16, 16, None, ctypes.byref(h)) == CORR_EINVAL
+    assert b"65535" in lib.corr_last_error()
     o = corr_opts(2, 1, 0, -1)  # FP16 has no CUDA-core X-engine
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
     assert not h.value
@@ -88,6 +92,26 @@ def test_null_handle_calls(lib):
 
 
 def test_int8_guard_boundary_is_exact():
-    # largest allowed n_spectra: 2 * 127^2 * n < 2^31
-    n = (2**31 - 1) // (2 * 127 * 127)
-    assert n == 66572 and 2 * 127 * 127 * n < 2**31 <= 2 * 127 * 127 * (n + 1)
+    # largest allowed n_spectra: 2 * 128^2 * n < 2^31 (an autocorrelation of -128 samples)
+    n = (2**31 - 1) // (2 * 128 * 128)
+    assert n == 65535 and 2 * 128 * 128 * n < 2**31 <= 2 * 128 * 128 * (n + 1)
+
+
+def test_batch_create_rejects_bad_arguments_without_device(lib):
+    from paper_1305_5639_gb300._lib import (corr_opts, corr_sub_desc, CORR_EINVAL, CORR_EOVERFLOW,
+                                            CORR_EUNSUPPORTED)
+
+    b = ctypes.c_void_p()
+    fake = 1 << 20  # 16-byte aligned stand-in addresses: never dereferenced before the checks fail
+    arr = (corr_sub_desc * 1)(corr_sub_desc(64, 4, 64, 0, fake, fake))
+    assert lib.corr_batch_create(0, arr, None, ctypes.byref(b)) == CORR_EINVAL
+    assert lib.corr_batch_create(1, arr, None, None) == CORR_EINVAL
+    o = corr_opts(0, 0, 0, -1)  # FP32 is not batched
+    assert lib.corr_batch_create(1, arr, ctypes.byref(o), ctypes.byref(b)) == CORR_EUNSUPPORTED
+    o = corr_opts(1, 1, 0, -1)  # nor is the CUDA-core X-engine
+    assert lib.corr_batch_create(1, arr, ctypes.byref(o), ctypes.byref(b)) == CORR_EUNSUPPORTED
+    bad = (corr_sub_desc * 1)(corr_sub_desc(64, 4, 65536, 0, fake, fake))  # INT32 guard with -128
+    assert lib.corr_batch_create(1, bad, None, ctypes.byref(b)) == CORR_EOVERFLOW
+    bad = (corr_sub_desc * 1)(corr_sub_desc(64, 4, 60, 0, fake, fake))  # spectra not a multiple of 8
+    assert lib.corr_batch_create(1, bad, None, ctypes.byref(b)) == CORR_EUNSUPPORTED
+    assert not b.value

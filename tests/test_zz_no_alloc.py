@@ -28,6 +28,15 @@ def test_noalloc_rejects_sizes_beyond_its_static_scratch():
     assert lib.corr_fengine_power_noalloc(dummy, 4, 4096, 8, 1, dummy, None) == CORR_EINVAL
     assert b"1024-channel static scratch" in lib.corr_last_error()
     assert lib.corr_fengine_power_noalloc(None, 4, 256, 8, 1, dummy, None) == CORR_EINVAL
+    assert b"null" in lib.corr_last_error()
+    # more inputs than the F-engine grid holds: a clean argument error, not a launch failure
+    assert lib.corr_fengine_power_noalloc(dummy, 65536, 256, 8, 1, dummy, None) == CORR_EINVAL
+    assert b"65535" in lib.corr_last_error()
+    # precision and alignment rejections carry their own message
+    assert lib.corr_fengine_power_noalloc(dummy, 4, 256, 8, 2, dummy, None) == CORR_EINVAL
+    assert b"precision" in lib.corr_last_error()
+    assert lib.corr_fengine_power_noalloc(ctypes.c_void_p(24), 4, 256, 8, 1, dummy, None) == CORR_EINVAL
+    assert b"aligned" in lib.corr_last_error()
 
 
 @pytest.mark.gpu
