@@ -3,7 +3,16 @@
 One step = F-engine (FFT + int8 re-packing + corner turn) + X-engine (INT8,
 exact) + integration dump to FP64, over one integration of the INT8 workload:
 256 antennas x 2 pol = 512 inputs, 1024 channels, 4096 spectra (4.29 GB of raw
-complex int8 voltages per step, larger than L2, so no flush is needed).
+complex int8 voltages per step, larger than L2, so no flush is needed). The
+JSON line's headline is that workload; after its timed region the default run
+adds compact sub-results for the other configurations (FP32 FX, FP16 plain and
+hi/lo, calibration forward + adjoint, batched sub-arrays) under "configs", each
+with its stage times, roofline fraction and accuracy (``--configs`` selects
+them; ``--workload A|C|D|E`` runs one alone).
+
+The ``small``, ``prof`` and ``prof_f`` workloads and ``--only-short-time`` are
+smaller INT8 shapes and a single-kernel mode for profiler captures, which must
+stay a few GB on the device; they are not bench lines.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on
 a bounded sample of the same workload instead.
@@ -245,7 +254,7 @@ def run_ours(args):
     volt_pin = torch.from_numpy(volt_h).pin_memory()
     volt = volt_pin.to(dev, non_blocking=False)
     planar = args.layout == "planar"
-    fused = planar and args.fused_dump
+    fused = args.fused_dump
     corr = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine=args.xengine, planar=planar,
                           fused_dump=fused)
     chan = corr.chan_buffer()
@@ -283,6 +292,9 @@ def run_ours(args):
         step()
     corr.check_status()
     torch.cuda.synchronize()
+    # count the library's kernel launches in the timed region (stage timing off: counts only)
+    corr.set_stage_timing(False)
+    corr.stage_times()
 
     evs = [[ev() for _ in range(4)] for _ in range(args.steps)]
     clk = ClockSampler(dev.index)
@@ -302,6 +314,7 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = clk.stop()
     corr.check_status()
+    launches = sum(n for _, n in corr.stage_times().values())
     ms = t0.elapsed_time(t1)
     f_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     x_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
@@ -384,7 +397,7 @@ def run_ours(args):
         r_cmac = float(N) * h2 * (n_in - h2) * K
         pk = _peaks()
         cross = {"inputs": f"[0, {h2}) x [{h2}, {n_in})", "ms": r_ms, "cmac_per_s": r_cmac / (r_ms * 1e-3),
-                 "tensor_frac": 8.0 * r_cmac / (r_ms * 1e-3) / 1e12 / pk["bf16_sus"]}
+                 "tensor_frac": 8.0 * r_cmac / (r_ms * 1e-3) / 1e12 / pk["bf16"]}
         del rect
 
     # ---- CUDA-core comparator at the same accuracy (exact dp4a INT8 X-engine), same data
@@ -402,36 +415,43 @@ def run_ours(args):
         torch.cuda.synchronize()
         cc_ms = a.elapsed_time(b)
         cc.close()
+        del chan8
 
     if rank != 0:
+        corr.close()
         if ws > 1:
             torch.distributed.destroy_process_group()
         return 0
 
     peaks = _peaks()
     x_flops = 8.0 * cmac_step
-    # read complex int8 voltages + write the channelised data (2 B/complex int8, 4 B planar FP16)
-    f_bytes = float(n_in * N * K * 2 + chan.numel() * chan.element_size())
-    tensor = corr_uses_tc(args.xengine)
+    # algorithmic F-engine bytes (the survey's unit): read the complex int8 voltages and
+    # write complex int8 spectra once, 2 B + 2 B per complex sample
+    f_bytes = float(n_in * N * K * 4)
+    # bytes the chosen exchange layout moves: the planar FP16 codes are 4 B per sample
+    f_layout_bytes = float(n_in * N * K * 2 + chan.numel() * chan.element_size())
     full_size = args.workload == "B"
     x_ach = x_flops / (x_ms * 1e-3) / 1e12
     f_ach = f_bytes / (f_ms * 1e-3) / 1e9
-    if tensor:
-        roof_x = {"bound": "tensor", "achieved": x_ach, "peak": peaks["bf16_sus"], "unit": "TFLOP/s",
-                  "frac": x_ach / peaks["bf16_sus"],
-                  "traffic": _traffic("k_xeng_tma") if (full_size and planar) else None,
-                  "kernel": "k_xeng_tma (X-engine INT8-exact, tcgen05 kind::f16)" if planar
-                  else "k_xeng_tc (X-engine INT8-exact, tcgen05 kind::f16)",
-                  "peak_note": f"{peaks['src']} sustained bf16 dense (fp16 runs at the same rate)",
-                  "algorithmic": f"{x_flops:.4g} FLOP per launch (8 per complex MAC over packed baselines)"}
-    else:
+    roof_x = {"bound": "tensor", "achieved": x_ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
+              "frac": x_ach / peaks["bf16"], "frac_of_sustained": x_ach / peaks["bf16_sus"],
+              "traffic": _traffic("k_xeng_tma") if (full_size and planar) else None,
+              "kernel": "k_xeng_tma (X-engine INT8-exact, tcgen05 kind::f16, wide form)",
+              "peak_note": f"{peaks['src']} burst bf16 dense (fp16 runs at the same rate; the kernel is timed "
+                           f"inside a region of well under a second)",
+              "algorithmic": f"{x_flops:.4g} FLOP per launch (8 per complex MAC over packed baselines)"}
+    if args.xengine == "cudacore":
         roof_x = {"bound": "alu", "achieved": x_ach, "peak": None, "unit": "TOP/s", "frac": None,
                   "traffic": None, "kernel": "k_xeng_i8 (CUDA-core dp4a)"}
+    f_traffic = _traffic("k_fengine") if (full_size and planar and not args.pfb and not args.delays) else None
     roof_f = {"bound": "hbm", "achieved": f_ach, "peak": peaks["hbm"], "unit": "GB/s", "frac": f_ach / peaks["hbm"],
-              "traffic": _traffic("k_fengine") if (full_size and planar) else None,
+              "traffic": f_traffic,
+              "traffic_ratio": None if f_traffic is None else f_traffic / f_bytes,
+              "layout_bytes": f_layout_bytes,
               "kernel": "k_fengine (FFT + int8 re-packing + corner turn)",
               "peak_note": f"{peaks['src']} HBM copy bandwidth",
-              "algorithmic": f"{f_bytes:.4g} bytes per launch (read raw int8, write channelised data once)"}
+              "algorithmic": f"{f_bytes:.4g} bytes per launch (read 2 B + write 2 B per complex sample); the "
+                             f"{args.layout} exchange layout moves {f_layout_bytes:.4g}"}
     d_bytes = float(N * B * (8 + 32))  # read INT32 pairs, read and write FP64 pairs
     roof_d = None
     if d_ms:
@@ -442,13 +462,27 @@ def run_ours(args):
                   "peak_note": f"{peaks['src']} HBM copy bandwidth",
                   "algorithmic": f"{d_bytes:.4g} bytes per launch (40 per visibility)"}
     roof = roof_f if f_ms >= x_ms else roof_x
+
+    # ---- the other configurations (rank 0 at one GPU): free this workload's buffers first
+    configs = None
+    if ws == 1 and args.configs:
+        corr.close()
+        del chan, volt
+        torch.cuda.empty_cache()
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        configs = {}
+        runners = {"A": lambda: bench_A(10, 3, dev, peaks, mhz),
+                   "C": lambda: bench_C(2, 1, dev, peaks, args.c_window),
+                   "D": lambda: bench_D(10, 3, dev, peaks, bool(args.comparator)),
+                   "E": lambda: bench_E(10, 3, dev, peaks, args.e_window)}
+        for name in args.configs:
+            configs[name] = runners[name]()
+            torch.cuda.empty_cache()
     cpu = None
     if ws == 1 and not args.no_cpu:
         # about 10 s of host work on 16 cores (24 of the 1024 channels, all inputs and spectra)
         r, dt, cores, desc = cpu_oracle_sample(n_ant, n_pol, N, K, n_chan_sample=24, volt=volt_h)
         cpu = {"value": r, "unit": "cMAC/s", "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
-    # per step: F-engine, X-engine (+ dump kernel unless fused); the calibration power pass is outside
-    launches = 2 if fused else 3
     line = {
         "metric": METRIC, "value": value, "unit": "cMAC/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -460,10 +494,10 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "stages_ms": {"fengine": f_ms, "xengine": x_ms, "dump": d_ms},
         "xengine_cmac_per_s": cmac_step / (x_ms * 1e-3),
-        "fengine_gbs": f_bytes / (f_ms * 1e-3) / 1e9,
-        "fengine_hbm_frac": f_bytes / (f_ms * 1e-3) / 1e9 / peaks["hbm"],
+        "fengine_gbs": f_ach,
+        "fengine_hbm_frac": f_ach / peaks["hbm"],
         "fengine_fp32": fengine_fp32_rate(N, n_in * K, f_ms, clocks),
-        "dump_gbs": (N * B * (8 + 32)) / (d_ms * 1e-3) / 1e9,
+        "dump_gbs": d_bytes / (d_ms * 1e-3) / 1e9 if d_ms else None,
         "cudacore_comparator": None if cc_ms is None else {
             "xengine_ms": cc_ms, "cmac_per_s": cmac_step / (cc_ms * 1e-3), "speedup_tensor_vs_cudacore": cc_ms / x_ms,
             "accuracy": "both exact (bit-identical INT32)"},
@@ -473,16 +507,18 @@ def run_ours(args):
         "roofline_xengine": roof_x,
         "roofline_fengine": roof_f,
         "roofline_dump": roof_d,
+        "configs": configs,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * cmac_step / (e2e_ms * 1e-3), "unit": "cMAC/s",
-                "h2d_bytes_per_step": int(volt.numel()), "d2h_bytes_per_step": int(vis_pin.numel() * 16),
+                "h2d_bytes_per_step": int(volt_pin.numel()), "d2h_bytes_per_step": int(vis_pin.numel() * 16),
                 "ms_per_step": e2e_ms, "ms_per_step_min": float(min(e2e_blocks)), "ms_per_step_blocks": e2e_blocks,
                 "path": "corr_fx_host (copies pipelined with the engines)" if planar else "copies then kernels"},
-        "gpu_launches": launches * args.steps,
+        "gpu_launches": launches,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
-    corr.close()
+    if not (ws == 1 and args.configs):
+        corr.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -530,105 +566,221 @@ def run_short_time_only(args):
     return 0
 
 
-def run_batched(args):
-    """Batched workload: 64 sub-arrays (antennas log-uniform 32-2048, channels from
-    {256, 1024, 4096}, 512-4096 spectra, complex int8 sigma=16 as planar FP16
-    codes), each on a window of --window channels (the full set, ~490 GB, does not
-    fit one GPU). One tuned, graph-replayed persistent launch against 64 sequential
-    plain launches of the same data."""
-    import tempfile
+# ----------------------------------------------------------------------------- the other configurations
+# Compact sub-results for the FP32 FX, FP16, calibration and batched workloads, run
+# after the INT8 workload's timed region (rank 0, one GPU) and reported beside it.
+# Each gives its time, complex-MAC/s, roofline fraction of the dominant kernel,
+# per-stage kernel times from the library's stage timing, and the accuracy against
+# an FP64 reference computed on the GPU with torch (cuFFT / cuBLAS in complex128:
+# a measurement beside the number; the parity proof is the test suite's oracle).
 
+
+def _ev():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True)
+
+
+def _flush_l2(buf):
+    """Overwrite a buffer larger than L2 (129 MB) so that the next step starts cold."""
+    buf.zero_()
+
+
+def _packed_from_full(Vfull):
+    """[n_chan, n, n] -> packed lower triangle [n_chan, B] (b(i, j) = i (i + 1) / 2 + j)."""
+    import torch
+
+    n = Vfull.shape[-1]
+    i, j = torch.tril_indices(n, n, device=Vfull.device)
+    return Vfull[:, i, j]
+
+
+def _norm_err(V, Vref, n_in):
+    """max and rms of |V_ij - Vref_ij| / sqrt(|Vref_ii| |Vref_jj|) over packed pairs."""
+    import torch
+
+    idx = torch.arange(n_in, device=Vref.device)
+    aut = Vref[:, idx * (idx + 1) // 2 + idx].abs()
+    i, j = torch.tril_indices(n_in, n_in, device=Vref.device)
+    e = (V.to(torch.complex128) - Vref).abs() / torch.sqrt(aut[:, i] * aut[:, j])
+    return float(e.max()), float(torch.sqrt((e ** 2).mean()))
+
+
+def _stage_ms(times, steps):
+    return {k: v[0] / steps for k, v in times.items() if v[1]}
+
+
+def _stage_launches(times, steps):
+    return {k: v[1] // steps for k, v in times.items() if v[1]}
+
+
+def bench_A(steps, warmup, dev, peaks, clocks_mhz):
+    """FP32 FX (16 antennas x 1 pol, 256-point FFT, 1024 spectra, complex64 N(0,1)
+    plus a source delayed by d_i = i samples): F-engine FFT + FP32 CUDA-core X-engine
+    + dump per step, L2 flushed before each step (the whole workload, 33.5 MB,
+    would otherwise sit in L2)."""
     import torch
 
     import synth
-    from paper_1305_5639_gb300 import build as pbuild
-
-    pbuild.build()
     from paper_1305_5639_gb300 import api
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    subs = synth.subarrays(seed=0)
-    W = args.window
-    gen = torch.Generator(device=dev).manual_seed(0)
-    planes = []
-    for d in subs:
-        z = torch.randn((W, 2, d["n_in"], d["n_spectra"]), generator=gen, device=dev) * 16.0
-        planes.append(torch.clamp(torch.round(z), -127, 127).to(torch.float16).contiguous())
-    cmac = float(sum(W * d["n_in"] * (d["n_in"] + 1) // 2 * d["n_spectra"] for d in subs))
+    n_in, N, K = 16, 256, 1024
+    B = n_in * (n_in + 1) // 2
+    v = torch.from_numpy(synth.volt_fp32(n_in, N, K, seed=0)).to(dev)
+    c = api.Correlator(n_in, 1, N, K, precision="fp32")
+    chan = c.chan_buffer()
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MB
     stream = torch.cuda.current_stream()
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    b = api.Batch(planes)
-    cache = os.path.join(tempfile.gettempdir(), "corr_batch_tune.json")
-    b.tune(cache)
-    seq = [api.Correlator(d["n_in"], 1, W, d["n_spectra"], precision="int8", planar=True) for d in subs]
+    def step():
+        c.fengine(v, None, chan)
+        c.xengine(chan)
+        c.dump(copy=False)
 
-    def run_seq():
-        for c, p in zip(seq, planes):
-            c.xengine(p)
-            c.dump(copy=False)
-
-    for _ in range(args.warmup):
-        b.run()
-        run_seq()
-    b.check_status()
-    torch.cuda.synchronize()
-    clk = ClockSampler(dev.index)
-    clk.start()
-    time.sleep(0.3)
-    a0, a1 = ev(), ev()
-    a0.record(stream)
-    for _ in range(args.steps):
-        b.run()
-    a1.record(stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    t_batch = a0.elapsed_time(a1) / args.steps
-    a0.record(stream)
-    for _ in range(args.steps):
-        run_seq()
-    a1.record(stream)
-    torch.cuda.synchronize()
-    t_seq = a0.elapsed_time(a1) / args.steps
-    b.check_status()
-    peaks = _peaks()
-    ach = 8.0 * cmac / (t_batch * 1e-3) / 1e12
-    line = {
-        "metric": METRIC, "value": cmac / (t_batch * 1e-3), "unit": "cMAC/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-        "config": {"workload": f"batched: 64 sub-arrays (seed-0 shapes), {W}-channel window each, complex int8 "
-                               f"sigma=16 as planar FP16 codes, one tuned graph-replayed persistent launch",
-                   "l2": f"inputs larger than L2 ({sum(p.numel() * 2 for p in planes) / 1e9:.2f} GB per step)"},
-        "sequential_64_launches_ms": t_seq, "speedup_vs_sequential": t_seq / t_batch,
-        "channels_per_tile": [b.channels_per_tile(k) for k in range(len(subs))],
-        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_sus"], "unit": "TFLOP/s",
-                     "frac": ach / peaks["bf16_sus"], "traffic": None, "kernel": "k_xeng_tma (batched)"},
-        "gpu_launches": args.steps, "clocks": clocks,
+    for _ in range(warmup):
+        step()
+    c.set_stage_timing(True)
+    c.stage_times()
+    tot = 0.0
+    for _ in range(steps):
+        _flush_l2(flush)
+        a, b = _ev(), _ev()
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    st = c.stage_times()
+    ms = tot / steps
+    # accuracy of one integration against FP64 on the GPU (cuFFT + complex128 products)
+    c.reset()
+    c.fengine(v, None, chan)
+    c.xengine(chan)
+    V = c.accum()
+    S = torch.fft.fft(v.to(torch.complex128).reshape(n_in, K, N), dim=-1)  # [i, a, k]
+    Vref = _packed_from_full(torch.einsum("iak,jak->kij", S, S.conj()))
+    emax, erms = _norm_err(V, Vref, n_in)
+    c.check_status()
+    c.close()
+    cm = N * B * K
+    x_ms = st["xengine"][0] / steps
+    fp32_peak = FP32_FLOP_PER_CLK * clocks_mhz * 1e6 / 1e12
+    f_bytes = n_in * N * K * 16.0  # read and write 8 B per complex sample
+    return {
+        "workload": "FP32 FX: 16 antennas x 1 pol, 256-point FFT, 1024 spectra, complex64 N(0,1) + source delayed "
+                    "d_i = i samples",
+        "ms_per_step": ms, "cmac_per_s": cm / (ms * 1e-3),
+        "stages_ms": _stage_ms(st, steps), "launches_per_step": _stage_launches(st, steps),
+        "roofline": {"kernel": "k_xeng_f32 (FP32 CUDA-core X-engine)", "bound": "alu",
+                     "achieved": 8.0 * cm / (x_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": 8.0 * cm / (x_ms * 1e-3) / 1e12 / fp32_peak,
+                     "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop at {clocks_mhz:.0f} MHz"},
+        "fengine_gbs": f_bytes / (st["fengine"][0] / steps * 1e-3) / 1e9,
+        "note": "launch-bound size (a few microseconds per kernel); L2 flushed before each step",
+        "err_vs_fp64": {"max": emax, "rms": erms, "bar": 1e-5,
+                        "reference": "torch complex128 on the GPU: cuFFT of the raw voltages, then X X^H"},
     }
-    print(json.dumps(line), flush=True)
-    b.close()
-    for c in seq:
+
+
+def bench_C(steps, warmup, dev, peaks, window):
+    """FP16 workload (1024 antennas x 2 pol = 2048 inputs, 2048 spectra per
+    integration, 8 integrations dumped to FP64) on a window of `window` of the 4096
+    channels (the per-channel work is the same; all channels would hold 137 GB of
+    complex64 input). hi/lo and plain FP16 on the tensor cores, each step = 8
+    integrations of the window; the FP32 CUDA-core X-engine once for comparison."""
+    import torch
+
+    from paper_1305_5639_gb300 import api
+
+    n_ant, n_pol, K, n_int = 1024, 2, 2048, 8
+    n_in = n_ant * n_pol
+    W = window
+    B = n_in * (n_in + 1) // 2
+    gen = torch.Generator(device=dev).manual_seed(0)
+    X = torch.complex(torch.randn((W, n_in, K), generator=gen, device=dev),
+                      torch.randn((W, n_in, K), generator=gen, device=dev)).contiguous()
+    stream = torch.cuda.current_stream()
+    res = {}
+    for prec in ("fp16_hilo", "fp16"):
+        c = api.Correlator(n_ant, n_pol, W, K, precision=prec)
+
+        def step():
+            for _ in range(n_int):
+                c.xengine(X)
+                c.dump(copy=False)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        c.set_stage_timing(True)
+        c.stage_times()
+        a, b = _ev(), _ev()
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        st = c.stage_times()
+        c.check_status()
         c.close()
-    return 0
+        res[prec] = (a.elapsed_time(b) / steps, st)
+    # accuracy on 2 channels, one integration: each path against FP64 (cuBLAS complex128)
+    Xe = X[:2].contiguous()
+    Xd = Xe.to(torch.complex128)
+    Vref = _packed_from_full(torch.matmul(Xd, Xd.conj().transpose(1, 2)))
+    del Xd
+    errs = {}
+    for prec, xe in (("fp16_hilo", "auto"), ("fp16", "auto"), ("fp32", "cudacore")):
+        c = api.Correlator(n_ant, n_pol, 2, K, precision=prec, xengine=xe)
+        c.xengine(Xe)
+        errs[prec] = _norm_err(c.accum(), Vref, n_in)
+        if prec == "fp32":
+            torch.cuda.synchronize()
+            a, b = _ev(), _ev()
+            a.record(stream)
+            c.xengine(Xe)
+            b.record(stream)
+            torch.cuda.synchronize()
+            cc_ms_per_chan_int = a.elapsed_time(b) / 2
+        c.close()
+    del X, Xe
+    cm = W * B * K * n_int
+    out = {"workload": f"FP16: 2048 inputs, 2048 spectra x 8 integrations dumped to FP64, window of {W} of 4096 "
+                       f"channels, complex64 N(0,1)", "window_channels": W}
+    for prec, (ms, st) in res.items():
+        x_ms = st["xengine"][0] / steps
+        ach = 8.0 * cm / (x_ms * 1e-3) / 1e12
+        executed = 3 if prec == "fp16_hilo" else 1
+        out[prec] = {
+            "ms_per_step": ms, "cmac_per_s": cm / (ms * 1e-3),
+            "stages_ms": _stage_ms(st, steps), "launches_per_step": _stage_launches(st, steps),
+            "xengine_cmac_per_s": cm / (x_ms * 1e-3),
+            "roofline_xengine": {"kernel": f"k_xeng_tma<FP16, {4 if prec == 'fp16_hilo' else 2} planes>",
+                                 "bound": "tensor", "achieved": ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
+                                 "frac": ach / peaks["bf16"], "frac_executed": executed * ach / peaks["bf16"],
+                                 "peak_note": f"{peaks['src']} burst bf16 dense (fp16 runs at the same rate)"},
+            "err_vs_fp64": {"max": errs[prec][0], "rms": errs[prec][1],
+                            "bar": 5e-5 if prec == "fp16_hilo" else 2e-3},
+        }
+    cc_ms = cc_ms_per_chan_int * W * n_int
+    out["fp32_cudacore"] = {"ms_per_step_extrapolated": cc_ms, "cmac_per_s": cm / (cc_ms * 1e-3),
+                            "timed": "one integration of 2 channels, scaled to the window's 8 integrations",
+                            "err_vs_fp64": {"max": errs["fp32"][0], "rms": errs["fp32"][1], "bar": 1e-5},
+                            "hilo_speedup": cc_ms / res["fp16_hilo"][0]}
+    out["err_reference"] = "torch complex128 X X^H on the GPU (cuBLAS), 2 channels, one integration"
+    return out
 
 
-def run_calibration(args):
-    """Calibration workload: 512 inputs, 1024 channels, 1024 spectra, per-input
-    complex gains; one gained forward X-engine and one adjoint (dL/dX and dL/dg)
-    per step. The headline runs both on tcgen05 tensor cores with the FP16 hi/lo
-    split; the FP32 CUDA-core forward and adjoint are timed beside it."""
+def bench_D(steps, warmup, dev, peaks, comparator=True):
+    """Calibration workload: 512 inputs, 1024 channels, 1024 spectra, complex64,
+    per-input complex gains; one gained forward X-engine (hi/lo, tensor cores) and
+    one adjoint (dL/dX, dL/dg on tensor cores) per step. The FP32 CUDA-core forward
+    and adjoint run once beside it; the gradients are compared with each other."""
     import torch
 
     import synth
-    from paper_1305_5639_gb300 import build as pbuild
-
-    pbuild.build()
     from paper_1305_5639_gb300 import api
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
     n_in, N, K = 512, 1024, 1024
     B = n_in * (n_in + 1) // 2
     gen = torch.Generator(device=dev).manual_seed(0)
@@ -640,9 +792,8 @@ def run_calibration(args):
     gx = torch.empty_like(X)
     gg = torch.empty(n_in, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream()
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def measure(precision):
+    def measure(precision, n_steps, n_warm):
         c = api.Correlator(n_in, 1, N, K, precision=precision)
 
         def fwd():
@@ -652,130 +803,149 @@ def run_calibration(args):
         def bwd():
             api.corr_backward(c.h, G, X, g, gx, gg)
 
-        for _ in range(args.warmup):
+        for _ in range(n_warm):
             fwd()
             bwd()
         torch.cuda.synchronize()
-        res = {}
+        c.set_stage_timing(True)
+        c.stage_times()
+        r = {}
         for name, fn in (("forward", fwd), ("backward", bwd)):
-            a, b = ev(), ev()
+            a, b = _ev(), _ev()
             a.record(stream)
-            for _ in range(args.steps):
+            for _ in range(n_steps):
                 fn()
             b.record(stream)
             torch.cuda.synchronize()
-            res[name] = a.elapsed_time(b) / args.steps
+            r[name] = a.elapsed_time(b) / n_steps
+        st = c.stage_times()
         c.check_status()
         c.close()
-        return res
+        return r, st, gx.clone(), gg.clone()
 
-    tc = measure("fp16_hilo")
-    cc = measure("fp32") if args.comparator else None
+    tc, st, dX_tc, dg_tc = measure("fp16_hilo", steps, warmup)
     cm_f, cm_b = N * B * K, N * n_in * n_in * K
     ms = tc["forward"] + tc["backward"]
-    # launches per step: forward planar split + X-engine + dump; adjoint: 4 per block of
-    # channels (exponents, A planes, conj(X)^T planes, GEMM) + 2 for the dL/dg reduction
-    cb = max(1, min(N, (1 << 30) // (8 * n_in * n_in + 8 * K * n_in)))
-    launches = 3 + 4 * ((N + cb - 1) // cb) + 2
-    line = {
-        "metric": METRIC, "value": (cm_f + cm_b) / (ms * 1e-3), "unit": "cMAC/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16 hi/lo (f32 accumulate)",
-        "data": "synthetic",
-        "config": {"workload": "calibration: 512 inputs, 1024 channels, 1024 spectra, complex64, per-input gains; "
-                               "gained X-engine + adjoint (dL/dX, dL/dg)",
-                   "l2": "inputs larger than L2 (4.29 GB)"},
-        "forward_ms": tc["forward"], "forward_cmac_per_s": cm_f / (tc["forward"] * 1e-3),
-        "backward_ms": tc["backward"], "backward_cmac_per_s": cm_b / (tc["backward"] * 1e-3),
-        "cudacore_fp32": None if cc is None else {
-            "forward_ms": cc["forward"], "backward_ms": cc["backward"],
-            "speedup_step": (cc["forward"] + cc["backward"]) / ms},
-        "gpu_launches": launches * args.steps,
+    gemm_ms = st["adj_gemm"][0] / steps
+    ach = 8.0 * cm_b / (gemm_ms * 1e-3) / 1e12
+    out = {
+        "workload": "calibration: 512 inputs, 1024 channels, 1024 spectra, complex64, per-input gains; gained "
+                    "X-engine + adjoint (dL/dX, dL/dg)",
+        "ms_per_step": ms, "cmac_per_s": (cm_f + cm_b) / (ms * 1e-3),
+        "forward_ms": tc["forward"], "backward_ms": tc["backward"],
+        "stages_ms": _stage_ms(st, steps), "launches_per_step": _stage_launches(st, steps),
+        "roofline_adjoint_gemm": {"kernel": "k_xeng_tma<kAdj> (dX GEMM, hi/lo: 3 products)", "bound": "tensor",
+                                  "achieved": ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
+                                  "frac": ach / peaks["bf16"], "frac_executed": 3 * ach / peaks["bf16"],
+                                  "algorithmic": f"{8.0 * cm_b:.4g} FLOP per step (n_in^2 K complex MAC per "
+                                                 f"channel, 8 FLOP each)"},
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    if comparator:
+        cc, _, dX_cc, dg_cc = measure("fp32", 1, 1)
+        rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))  # noqa: E731
+        rms = torch.sqrt(torch.mean(dX_cc.abs() ** 2, dim=(1, 2)))
+        elem = float(torch.max(torch.amax((dX_tc - dX_cc).abs(), dim=(1, 2)) / rms))
+        out["fp32_cudacore"] = {"forward_ms": cc["forward"], "backward_ms": cc["backward"],
+                                "speedup_step": (cc["forward"] + cc["backward"]) / ms}
+        out["grad_vs_fp32"] = {"dX_rel_l2": rel(dX_tc, dX_cc), "dg_rel_l2": rel(dg_tc, dg_cc),
+                               "dX_max_over_channel_rms": elem, "bar_rel_l2": 1e-4}
+    del X, G, gx
+    return out
 
 
-def run_fp16(args):
-    """FP16 workload: 1024 antennas x 2 pol = 2048 inputs, 2048 spectra per integration,
-    8 integrations dumped to FP64, on a window of --window channels of the 4096 (the
-    per-channel work is identical; the full set would hold 137 GB of complex64 input).
-    One step = 8 integrations (X-engine + dump) of the window. The headline is the hi/lo
-    FP16 X-engine (FP32-class accuracy); plain FP16 and the FP32 CUDA-core X-engine are
-    timed on the same data."""
+def bench_E(steps, warmup, dev, peaks, window):
+    """Batched workload: 64 sub-arrays (antennas log-uniform 32-2048, channels from
+    {256, 1024, 4096}, 512-4096 spectra, complex int8 sigma=16 as planar FP16 codes),
+    each on a window of `window` channels (the full set, ~490 GB, does not fit one
+    GPU): one tuned, graph-replayed persistent launch against 64 sequential plain
+    launches of the same data (their results compared bit for bit)."""
+    import tempfile
+
+    import torch
+
+    import synth
+    from paper_1305_5639_gb300 import api
+
+    subs = synth.subarrays(seed=0)
+    W = window
+    gen = torch.Generator(device=dev).manual_seed(0)
+    planes = []
+    for d in subs:
+        z = torch.randn((W, 2, d["n_in"], d["n_spectra"]), generator=gen, device=dev) * 16.0
+        planes.append(torch.clamp(torch.round(z), -127, 127).to(torch.float16).contiguous())
+    cmac = float(sum(W * d["n_in"] * (d["n_in"] + 1) // 2 * d["n_spectra"] for d in subs))
+    stream = torch.cuda.current_stream()
+    b = api.Batch(planes)
+    b.tune(os.path.join(tempfile.gettempdir(), "corr_batch_tune.json"))
+    seq = [api.Correlator(d["n_in"], 1, W, d["n_spectra"], precision="int8", planar=True) for d in subs]
+
+    def run_seq():
+        for c, p in zip(seq, planes):
+            c.xengine(p)
+            c.dump(copy=False)
+
+    for _ in range(warmup):
+        b.run()
+        run_seq()
+    b.check_status()
+    torch.cuda.synchronize()
+    a0, a1 = _ev(), _ev()
+    a0.record(stream)
+    for _ in range(steps):
+        b.run()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = a0.elapsed_time(a1) / steps
+    a0.record(stream)
+    for _ in range(steps):
+        run_seq()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = a0.elapsed_time(a1) / steps
+    b.check_status()
+    # the batch's INT32 outputs against the sequential launches' accumulators
+    exact = True
+    for c, p, v in zip(seq, planes, b.vis):
+        c.reset()
+        c.xengine(p)
+        exact = exact and bool(torch.equal(c.accum(), v))
+        c.close()
+    cpt = [b.channels_per_tile(k) for k in range(len(subs))]
+    b.close()
+    ach = 8.0 * cmac / (t_batch * 1e-3) / 1e12
+    return {
+        "workload": f"batched: 64 sub-arrays (seed-0 shapes), {W}-channel window each, complex int8 sigma=16 as "
+                    f"planar FP16 codes, one tuned graph-replayed persistent launch",
+        "window_channels": W, "ms_per_step": t_batch, "cmac_per_s": cmac / (t_batch * 1e-3),
+        "sequential_64_launches_ms": t_seq, "speedup_vs_sequential": t_seq / t_batch,
+        "channels_per_tile": cpt, "bit_identical_to_sequential": exact,
+        "roofline": {"kernel": "k_xeng_tma (batched, wide INT8)", "bound": "tensor", "achieved": ach,
+                     "peak": peaks["bf16"], "unit": "TFLOP/s", "frac": ach / peaks["bf16"]},
+        "launches_per_step": 1,
+    }
+
+
+def _standalone(args, name, fn):
+    """One configuration alone: its sub-result as the JSON line's body."""
     import torch
 
     from paper_1305_5639_gb300 import build as pbuild
 
     pbuild.build()
-    from paper_1305_5639_gb300 import api
-
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    n_ant, n_pol, K, n_int = 1024, 2, 2048, 8
-    n_in = n_ant * n_pol
-    W = args.window
-    B = n_in * (n_in + 1) // 2
-    gen = torch.Generator(device=dev).manual_seed(0)
-    X = torch.complex(torch.randn((W, n_in, K), generator=gen, device=dev),
-                      torch.randn((W, n_in, K), generator=gen, device=dev)).contiguous()
-    stream = torch.cuda.current_stream()
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-
-    def measure(precision, steps, warmup):
-        # separate dump kernel: measured faster than the dump fused into the FP16 epilogues
-        # (40.0 / 43.4 ms vs 25.6 / 13.5 ms per step for hi/lo / plain), whose FP64 adds
-        # then stall the tensor pipe on GB300's reduced FP64 path
-        c = api.Correlator(n_ant, n_pol, W, K, precision=precision)
-
-        def step():
-            for _ in range(n_int):
-                c.xengine(X)
-                c.dump(copy=False)
-
-        for _ in range(warmup):
-            step()
-        torch.cuda.synchronize()
-        a, b = ev(), ev()
-        a.record(stream)
-        for _ in range(steps):
-            step()
-        b.record(stream)
-        torch.cuda.synchronize()
-        c.check_status()
-        c.close()
-        return a.elapsed_time(b) / steps
-
+    peaks = _peaks()
     clk = ClockSampler(0)
     clk.start()
-    hl = measure("fp16_hilo", args.steps, args.warmup)
+    r = fn(dev, peaks)
     clocks = clk.stop()
-    pl = measure("fp16", args.steps, args.warmup)
-    cc = measure("fp32", 1, 1) if args.comparator else None
-    cm = W * B * K * n_int
-    peaks = _peaks()
-    ach = 8.0 * cm / (hl * 1e-3) / 1e12
-    line = {
-        "metric": METRIC, "value": cm / (hl * 1e-3), "unit": "cMAC/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": hl, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f16 hi/lo (f32 accumulate)", "data": "synthetic",
-        "config": {"workload": f"FP16: 1024 antennas x 2 pol = 2048 inputs, 2048 spectra per integration, "
-                               f"8 integrations dumped to FP64, window of {W} of 4096 channels, complex64 N(0,1)",
-                   "l2": f"inputs larger than L2 ({X.numel() * 8 / 1e9:.2f} GB)"},
-        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_sus"], "unit": "TFLOP/s",
-                     "frac": ach / peaks["bf16_sus"], "traffic": None,
-                     "kernel": "k_to_planar + k_xeng_tma<FP16, 4 planes> + k_dump (hi/lo: 12 MMAs per 16 spectra, "
-                               "3x the algorithmic products)",
-                     "peak_note": f"{peaks['src']} sustained bf16 dense",
-                     "algorithmic": "8 FLOP per complex MAC over packed baselines"},
-        "fp16_plain": {"ms_per_step": pl, "cmac_per_s": cm / (pl * 1e-3),
-                       "tensor_frac": 8.0 * cm / (pl * 1e-3) / 1e12 / peaks["bf16_sus"]},
-        "cudacore_fp32": None if cc is None else {"ms_per_step": cc, "cmac_per_s": cm / (cc * 1e-3),
-                                                 "hilo_speedup": cc / hl},
-        "e2e": None,
-        "gpu_launches": 3 * n_int * args.steps,
-        "clocks": clocks,
-    }
+    unit_ms = r.get("ms_per_step") or r.get("fp16_hilo", {}).get("ms_per_step")
+    rate = r.get("cmac_per_s") or r.get("fp16_hilo", {}).get("cmac_per_s")
+    line = {"metric": METRIC, "value": rate, "unit": "cMAC/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": unit_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"A": "f32", "C": "f16 hi/lo (f32 accumulate)",
+                                            "D": "f16 hi/lo (f32 accumulate)", "E": "int8"}[name],
+            "data": "synthetic", "config": {"workload": r["workload"]}, "result": r, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -790,9 +960,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="B", choices=sorted(WORKLOADS) + ["C", "D", "E"])
-    ap.add_argument("--window", type=int, default=16,
-                    help="batched workload: channels per sub-array; FP16 workload: channels of the 4096 (use 32)")
+    ap.add_argument("--workload", default="B", choices=sorted(WORKLOADS) + ["A", "C", "D", "E"],
+                    help="B (default): the INT8 workload with the other configurations' sub-results; A, C, D, E: "
+                         "one configuration alone; small, prof, prof_f: smaller INT8 shapes for profiler captures")
+    ap.add_argument("--configs", default="ACDE",
+                    help="configurations whose sub-results the default run adds (subset of ACDE, '' for none)")
+    ap.add_argument("--c-window", type=int, default=256, help="FP16 workload: channels of the 4096 per step")
+    ap.add_argument("--e-window", type=int, default=16, help="batched workload: channels per sub-array")
     ap.add_argument("--xengine", default="auto", choices=["auto", "cudacore", "tcgen05"])
     ap.add_argument("--layout", default="planar", choices=["planar", "int8"],
                     help="channelised layout between the engines: planar FP16 codes (TMA X-engine) or complex int8")
@@ -818,12 +992,14 @@ def main():
         return run_reference(args)
     if args.only_short_time:
         return run_short_time_only(args)
-    if args.workload == "E":
-        return run_batched(args)
-    if args.workload == "D":
-        return run_calibration(args)
+    if args.workload == "A":
+        return _standalone(args, "A", lambda dev, pk: bench_A(args.steps, args.warmup, dev, pk, 2070.0))
     if args.workload == "C":
-        return run_fp16(args)
+        return _standalone(args, "C", lambda dev, pk: bench_C(args.steps, args.warmup, dev, pk, args.c_window))
+    if args.workload == "D":
+        return _standalone(args, "D", lambda dev, pk: bench_D(args.steps, args.warmup, dev, pk, args.comparator))
+    if args.workload == "E":
+        return _standalone(args, "E", lambda dev, pk: bench_E(args.steps, args.warmup, dev, pk, args.e_window))
     return run_ours(args)
 
 

@@ -54,17 +54,24 @@ enum {
     CORR_EUNSUPPORTED = 7  /* shape or mode not supported by this build */
 };
 
-/* Arithmetic of the X-engine. */
+/* Arithmetic of the X-engine. The FP16 forms first scale each (channel, input)
+ * row of the input by a power of two 2^e that brings its largest component into
+ * [2^14, 2^15) (exact, undone on the output), so that their accuracy does not
+ * depend on the data's magnitude. */
 enum {
     CORR_PREC_FP32 = 0,      /* float input, FP32 CUDA-core FFMA */
     CORR_PREC_INT8 = 1,      /* complex int8 input, exact integer result (INT32) */
     CORR_PREC_FP16 = 2,      /* float input rounded to FP16, FP32 accumulation (tensor cores) */
-    CORR_PREC_FP16_HILO = 3  /* float input split x = h + l into two FP16 parts, h = fp16(x),
-                                l = fp16(x - h); V ~ hh + hl + lh, FP32 accumulation (tensor cores) */
+    CORR_PREC_FP16_HILO = 3  /* float input split x 2^e = h + l into two FP16 parts, h = fp16(x 2^e),
+                                l = fp16(x 2^e - h); V ~ hh + hl + lh, FP32 accumulation (tensor cores) */
 };
 
 /* X-engine implementation. AUTO picks tcgen05 tensor cores for INT8/FP16/FP16_HILO
- * and CUDA cores for FP32. CUDACORE with INT8 uses exact dp4a integer arithmetic. */
+ * and CUDA cores for FP32 (TCGEN05 with FP32 is CORR_EUNSUPPORTED). The tensor-core
+ * X-engine reads planar FP16 operands by TMA: the caller's own (CORR_FLAG_PLANAR)
+ * or ones the library converts the input into, in a workspace allocated on first
+ * use (4 bytes per complex sample, 8 for FP16_HILO). CUDACORE with INT8 uses exact
+ * dp4a integer arithmetic. */
 enum { CORR_XENG_AUTO = 0, CORR_XENG_CUDACORE = 1, CORR_XENG_TCGEN05 = 2 };
 
 /* Layout flags (corr_opts.flags).
@@ -77,10 +84,10 @@ enum { CORR_XENG_AUTO = 0, CORR_XENG_CUDACORE = 1, CORR_XENG_TCGEN05 = 2 };
 enum { CORR_FLAG_PLANAR = 1 };
 
 /* CORR_FLAG_FUSED_DUMP: corr_xengine adds each integration straight into the FP64
- *   long-integration buffer from its epilogue. Valid with CORR_FLAG_PLANAR (INT8:
- *   the INT32 sums are exact, so the FP64 sums equal a separate dump's) and with
- *   CORR_PREC_FP16 / CORR_PREC_FP16_HILO on the AUTO X-engine with n_spectra % 8 == 0
- *   (the same FP32 tile sums a separate dump would add); CORR_EUNSUPPORTED otherwise.
+ *   long-integration buffer from its epilogue. Valid on the tensor-core X-engine
+ *   (INT8, FP16, FP16_HILO with xengine AUTO or TCGEN05): for INT8 the sums are
+ *   exact, so the FP64 sums equal a separate dump's; for FP16 the same FP32 tile
+ *   sums a separate dump would add. CORR_EUNSUPPORTED otherwise (FP32, CUDACORE).
  *   There is then no integration accumulator: corr_get_accum returns CORR_ESTATE,
  *   and corr_dump only copies the FP64 buffer out. */
 enum { CORR_FLAG_FUSED_DUMP = 2 };
@@ -193,8 +200,8 @@ CORR_API corr_status corr_fengine_power_noalloc(const void *volt, int32_t n_in, 
  * V'_ij[k] = g_i conj(g_j) sum_a X_a,i[k] conj(X_a,j[k]) (i >= j) into the
  * library-owned integration accumulator.
  *   chan_in [n_chan][n_in][n_spectra]: complex int8 for INT8, complex float
- *           otherwise (FP16 paths round or split it on the fly); with
- *           CORR_FLAG_PLANAR the planar FP16 layout. 16-byte aligned.
+ *           otherwise (the FP16 paths scale, round or split it in a conversion
+ *           pass); with CORR_FLAG_PLANAR the planar FP16 layout. 16-byte aligned.
  *   gains   [n_in] complex float, or NULL for unit gains. Not allowed with INT8
  *           (the INT8 result is an exact integer; CORR_EINVAL).
  * INT8: accumulator is INT32 per component; CORR_EOVERFLOW if the spectra
@@ -223,9 +230,9 @@ CORR_API corr_status corr_set_short_time(corr_t *h, int32_t block_spectra, int32
  *   vis_out [n_chan][n_p][n_q]: complex int32 (2 x int32) for INT8, complex float
  *           otherwise; 8-byte aligned device memory, overwritten.
  * chan_in and gains as for corr_xengine (gains: g_i conj(g_j), float precisions).
- * The handle's accumulator and long integration are not touched. INT8 needs
- * CORR_FLAG_PLANAR; FP16 / FP16_HILO the AUTO X-engine with n_spectra % 8 == 0;
- * otherwise CORR_EUNSUPPORTED. Ranges outside [0, n_in): CORR_EINVAL. */
+ * The handle's accumulator and long integration are not touched. Runs on the
+ * tensor-core X-engine (INT8, FP16, FP16_HILO; CORR_EUNSUPPORTED for FP32 and
+ * CUDACORE). Ranges outside [0, n_in): CORR_EINVAL. */
 CORR_API corr_status corr_xengine_cross(corr_t *h, const void *chan_in, const float *gains, int32_t p0,
                                         int32_t n_p, int32_t q0, int32_t n_q, void *vis_out, void *stream);
 
@@ -285,6 +292,35 @@ CORR_API corr_status corr_check_status(corr_t *h, void *stream);
  * CORR_ESTATE when the wait did not behave so, CORR_EINVAL for a limit out of range,
  * CORR_ECUDA on a CUDA error. */
 CORR_API corr_status corr_selftest_bounded_wait(int32_t device, int64_t limit_ns);
+
+/* Stages of the work a handle launches, for corr_stage_times (tracing; no
+ * counterpart in the paper). */
+enum {
+    CORR_STAGE_FENGINE = 0,    /* F-engine FFT + re-packing + corner turn (k_fengine) */
+    CORR_STAGE_PFB = 1,        /* polyphase filter bank FIR pass (k_pfb_fir) */
+    CORR_STAGE_POWER = 2,      /* per-channel power pass */
+    CORR_STAGE_PREP = 3,       /* conversion of the X-engine input to planar FP16 operands */
+    CORR_STAGE_XENGINE = 4,    /* X-engine (triangle or rectangle) */
+    CORR_STAGE_DUMP = 5,       /* integration dump into the FP64 long integration */
+    CORR_STAGE_ADJ_PREP = 6,   /* adjoint: scale exponents and operand planes */
+    CORR_STAGE_ADJ_GEMM = 7,   /* adjoint: the dX GEMM and its epilogue */
+    CORR_STAGE_ADJ_REDUCE = 8, /* adjoint: fixed-order dL/dg reduction */
+    CORR_STAGE_COUNT = 9
+};
+
+/* Per-stage timing of this handle's kernels (tracing). on != 0: every later call
+ * brackets each stage's launches with a pair of CUDA events on the stream the
+ * launches use (events are created on first use and kept); on == 0 stops
+ * recording. Recording costs two event records per stage and call. */
+CORR_API corr_status corr_set_stage_timing(corr_t *h, int32_t on);
+
+/* Read and clear the timing since the last read: ms[CORR_STAGE_COUNT] receives
+ * the summed event time per stage in milliseconds (overlapping stages on
+ * different streams both count), launches[CORR_STAGE_COUNT] (or NULL) the number
+ * of kernel launches per stage, counted whether or not timing is on. Waits for
+ * the recorded events (host-synchronous). CORR_ESTATE if more than 65536 stage
+ * records were made since the last read (the excess was not timed). */
+CORR_API corr_status corr_stage_times(corr_t *h, double *ms, int64_t *launches);
 
 /* Zero the accumulator and the FP64 long-integration buffer. */
 CORR_API corr_status corr_reset(corr_t *h, void *stream);

@@ -24,6 +24,7 @@ PREC = {"fp32": 0, "int8": 1, "fp16": 2, "fp16_hilo": 3}
 CORR_FLAG_PLANAR = 1
 CORR_FLAG_FUSED_DUMP = 2
 XENG = {"auto": 0, "cudacore": 1, "tcgen05": 2}
+STAGES = ("fengine", "pfb", "power", "prep", "xengine", "dump", "adj_prep", "adj_gemm", "adj_reduce")
 
 
 class corr_opts(ctypes.Structure):
@@ -63,6 +64,8 @@ SIGNATURES = [
     ("corr_fengine_power_noalloc", _S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         _P, _P]),
     ("corr_fx_host", _S, [_P, _P, _P, _P, _P]),
+    ("corr_set_stage_timing", _S, [_P, ctypes.c_int32]),
+    ("corr_stage_times", _S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     ("corr_batch_create", _S, [ctypes.c_int32, ctypes.POINTER(corr_sub_desc), ctypes.POINTER(corr_opts),
                                ctypes.POINTER(ctypes.c_void_p)]),
     ("corr_batch_tune", _S, [_P, ctypes.c_char_p, _P]),

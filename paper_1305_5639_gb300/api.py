@@ -253,6 +253,19 @@ class Correlator:
     def reset(self, stream=None):
         corr_reset(self.h, stream)
 
+    def set_stage_timing(self, on: bool = True):
+        """Bracket each stage's kernels with CUDA events (see stage_times)."""
+        check(_lib.load().corr_set_stage_timing(self.h, 1 if on else 0), "corr_set_stage_timing")
+
+    def stage_times(self):
+        """{stage: (milliseconds, kernel launches)} since the last read (then cleared);
+        waits for the recorded events."""
+        n = len(_lib.STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        check(_lib.load().corr_stage_times(self.h, ms, cnt), "corr_stage_times")
+        return {name: (float(ms[k]), int(cnt[k])) for k, name in enumerate(_lib.STAGES)}
+
     def backward(self, grad_vis, chan_in, gains=None, want_chan=True, want_gains=True, stream=None):
         gc = torch.empty_like(chan_in) if want_chan else None
         gg = torch.empty(self.n_in, dtype=torch.complex64, device=self.device) if want_gains else None

@@ -163,13 +163,18 @@ corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const fl
     const int nM = (h.n_in + TM - 1) / TM, nA = (h.n_spectra + TA - 1) / TA;
     if (h.n_chan > 65535) return CORR_EUNSUPPORTED;
     dim3 grid(nM, nA, h.n_chan);
-    k_adj<<<grid, NTH, 0, st>>>(grad_vis, chan_in, gains, grad_chan, grad_gains ? ws : nullptr, h.n_in,
-                                h.n_spectra, h.n_base);
-    corr_status s = check_launch("k_adj");
+    corr_status s;
+    {
+        StageScope sc(h, CORR_STAGE_ADJ_GEMM, st);
+        k_adj<<<grid, NTH, 0, st>>>(grad_vis, chan_in, gains, grad_chan, grad_gains ? ws : nullptr, h.n_in,
+                                    h.n_spectra, h.n_base);
+        s = check_launch("k_adj");
+    }
     if (s != CORR_OK || !grad_gains) return s;
     const long long n_part = (long long)h.n_chan * nA;
     double2 *scratch = reinterpret_cast<double2 *>(reinterpret_cast<char *>(ws) +
                                                    align16(sizeof(float2) * (size_t)n_part * h.n_in));
+    StageScope sc(h, CORR_STAGE_ADJ_REDUCE, st, 2);
     return launch_adj_reduce(ws, scratch, grad_gains, h.n_in, n_part, st);
 }
 

@@ -228,8 +228,12 @@ corr_status launch_backward_tc(const Handle &h, const float2 *grad_vis, const fl
     const int nt_in = (h.n_in + kTile - 1) / kTile, nt_k = (h.n_spectra + kTile - 1) / kTile;
     CORR_CUDA_TRY(cudaEventRecord(ev[0], st));
     CORR_CUDA_TRY(cudaStreamWaitEvent(side, ev[0], 0));
-    k_adj_expo<<<h.n_chan, 256, 0, side>>>(grad_vis, gains, expo, h.n_in, h.n_base, 0);
-    corr_status s = check_launch("k_adj_expo");
+    corr_status s;
+    {
+        StageScope sc(h, CORR_STAGE_ADJ_PREP, side);
+        k_adj_expo<<<h.n_chan, 256, 0, side>>>(grad_vis, gains, expo, h.n_in, h.n_base, 0);
+        s = check_launch("k_adj_expo");
+    }
     if (s != CORR_OK) return s;
     int blk = 0;
     for (int c0 = 0; c0 < h.n_chan; c0 += w.cb, ++blk) {
@@ -237,10 +241,14 @@ corr_status launch_backward_tc(const Handle &h, const float2 *grad_vis, const fl
         __half *A = reinterpret_cast<__half *>(base + w.a[k]);
         __half *Bt = reinterpret_cast<__half *>(base + w.b[k]);
         if (blk >= 2) CORR_CUDA_TRY(cudaStreamWaitEvent(side, ev[3 + k], 0));  // GEMM of block - 2 done
-        k_adj_aprep<<<dim3(nt_in, nt_in, nc), 256, 0, side>>>(grad_vis, gains, expo + c0, A, h.n_in, h.n_base, c0);
-        if ((s = check_launch("k_adj_aprep")) != CORR_OK) return s;
-        k_adj_bprep<<<dim3(nt_k, nt_in, nc), 256, 0, side>>>(chan_in, Bt, h.n_in, h.n_spectra, c0);
-        if ((s = check_launch("k_adj_bprep")) != CORR_OK) return s;
+        {
+            StageScope sc(h, CORR_STAGE_ADJ_PREP, side, 2);
+            k_adj_aprep<<<dim3(nt_in, nt_in, nc), 256, 0, side>>>(grad_vis, gains, expo + c0, A, h.n_in, h.n_base,
+                                                                 c0);
+            if ((s = check_launch("k_adj_aprep")) != CORR_OK) return s;
+            k_adj_bprep<<<dim3(nt_k, nt_in, nc), 256, 0, side>>>(chan_in, Bt, h.n_in, h.n_spectra, c0);
+            if ((s = check_launch("k_adj_bprep")) != CORR_OK) return s;
+        }
         CORR_CUDA_TRY(cudaEventRecord(ev[1 + k], side));
         CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + k], 0));
         s = launch_adjoint_tma(h, A, Bt, expo + c0, chan_in, gains, grad_chan, part, c0, c1, st);
@@ -249,6 +257,7 @@ corr_status launch_backward_tc(const Handle &h, const float2 *grad_vis, const fl
     }
     if (!grad_gains) return CORR_OK;
     const int nbj = (h.n_spectra + 127) / 128;
+    StageScope sc(h, CORR_STAGE_ADJ_REDUCE, st, 2);
     return launch_adj_reduce(part, reinterpret_cast<double2 *>(base + w.scratch), grad_gains, h.n_in,
                              (long long)h.n_chan * nbj * 2, st);
 }

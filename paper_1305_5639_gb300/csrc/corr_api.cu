@@ -31,7 +31,64 @@ corr_status check_launch(const char *what) {
     return CORR_OK;
 }
 
+StageScope::StageScope(const Handle &h, int stage, cudaStream_t st, int n_launch)
+    : c_(h.clock), stage_(stage), st_(st) {
+    if (!c_) return;
+    c_->launches[stage] += n_launch;
+    if (!c_->on) return;
+    if (c_->recs.size() >= StageClock::kMaxRecs) {
+        c_->overflow = true;
+        return;
+    }
+    if (c_->pool.empty()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        c_->pool.push_back(e);
+    }
+    a_ = c_->pool.back();
+    c_->pool.pop_back();
+    if (cudaEventRecord(a_, st_) != cudaSuccess) {
+        cudaGetLastError();
+        c_->pool.push_back(a_);
+        a_ = nullptr;
+    }
+}
+
+StageScope::~StageScope() {
+    if (!a_) return;
+    cudaEvent_t b = nullptr;
+    if (!c_->pool.empty()) {
+        b = c_->pool.back();
+        c_->pool.pop_back();
+    } else if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        c_->pool.push_back(a_);
+        return;
+    }
+    if (cudaEventRecord(b, st_) != cudaSuccess) {
+        cudaGetLastError();
+        c_->pool.push_back(a_);
+        c_->pool.push_back(b);
+        return;
+    }
+    c_->recs.push_back({stage_, a_, b});
+}
+
 namespace {
+
+void free_clock(Handle &h) {
+    if (!h.clock) return;
+    for (cudaEvent_t e : h.clock->pool) cudaEventDestroy(e);
+    for (const StageClock::Rec &r : h.clock->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    delete h.clock;
+    h.clock = nullptr;
+}
 
 // NVTX range around a C-ABI call (visible in a profiler's timeline; a no-op when no
 // tool is attached)
@@ -89,12 +146,53 @@ void free_buffers(Handle &h) {
     h.status = nullptr;
     h.power64 = nullptr;
     h.bwd_ws = nullptr;
+    free_clock(h);
 }
 
 bool use_tc(const Handle &h) {
     if (h.xengine == CORR_XENG_CUDACORE) return false;
-    if (h.xengine == CORR_XENG_TCGEN05) return true;
-    return h.precision != CORR_PREC_FP32;
+    return h.precision != CORR_PREC_FP32;  // FP32 has no tensor-core X-engine
+}
+
+// Planar FP16 operands of the tensor-core X-engine: the caller's buffer itself
+// (CORR_FLAG_PLANAR), or a conversion pass into the handle's workspace (complex
+// int8 codes: exact; complex float: FP16 or the hi/lo split, with per-row scaling).
+struct TcOperands {
+    const void *planes = nullptr;
+    int npl = 2;
+    const float *row_scale = nullptr;
+    int kstride = 0;
+};
+
+corr_status tc_operands(Handle &h, const void *chan_in, cudaStream_t st, TcOperands &op) {
+    if (!tma_available()) {
+        set_error_text("cuTensorMapEncodeTiled is not available from the driver");
+        return CORR_EUNSUPPORTED;
+    }
+    if (h.flags & CORR_FLAG_PLANAR) {
+        op.planes = chan_in;
+        op.kstride = h.n_spectra;
+        return CORR_OK;
+    }
+    op.npl = h.precision == CORR_PREC_FP16_HILO ? 4 : 2;
+    const size_t need = planar_ws_bytes(h, op.npl);
+    if (h.planar_ws_bytes < need) {
+        cudaFree(h.planar_ws);
+        h.planar_ws = nullptr;
+        h.planar_ws_bytes = 0;
+        if (cudaMalloc(&h.planar_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            set_error_text("allocating the planar FP16 operand workspace failed");
+            return CORR_ENOMEM;
+        }
+        h.planar_ws_bytes = need;
+    }
+    op.planes = h.planar_ws;
+    op.kstride = planar_kstride(h.n_spectra);
+    StageScope sc(h, CORR_STAGE_PREP, st);
+    if (h.precision == CORR_PREC_INT8) return launch_i8_to_planar(h, chan_in, h.planar_ws, st);
+    op.row_scale = planar_row_scale(h, h.planar_ws, op.npl);
+    return launch_to_planar(h, static_cast<const float2 *>(chan_in), h.planar_ws, op.npl, st);
 }
 
 }  // namespace
@@ -142,11 +240,11 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
     if (o.precision < CORR_PREC_FP32 || o.precision > CORR_PREC_FP16_HILO) return CORR_EINVAL;
     if (o.xengine < CORR_XENG_AUTO || o.xengine > CORR_XENG_TCGEN05) return CORR_EINVAL;
     if ((o.flags & ~(CORR_FLAG_PLANAR | CORR_FLAG_FUSED_DUMP)) != 0) return CORR_EINVAL;
-    // the dump fused into the X-engine epilogue exists on the TMA X-engine: INT8 planar,
-    // or FP16 / FP16 hi/lo (AUTO X-engine, n_spectra % 8 == 0)
-    const bool fp16_tma = (o.precision == CORR_PREC_FP16 || o.precision == CORR_PREC_FP16_HILO) &&
-                          o.xengine == CORR_XENG_AUTO && (n_spectra % 8) == 0;
-    if ((o.flags & CORR_FLAG_FUSED_DUMP) && !(o.flags & CORR_FLAG_PLANAR) && !fp16_tma) return CORR_EUNSUPPORTED;
+    // the dump fused into the X-engine epilogue exists on the tensor-core (TMA) X-engine:
+    // INT8, FP16 and FP16 hi/lo on the AUTO or TCGEN05 X-engine
+    if ((o.flags & CORR_FLAG_FUSED_DUMP) && (o.precision == CORR_PREC_FP32 || o.xengine == CORR_XENG_CUDACORE))
+        return CORR_EUNSUPPORTED;
+    if (o.precision == CORR_PREC_FP32 && o.xengine == CORR_XENG_TCGEN05) return CORR_EUNSUPPORTED;
     if ((o.flags & CORR_FLAG_PLANAR) &&
         (o.precision != CORR_PREC_INT8 || o.xengine == CORR_XENG_CUDACORE || (n_spectra % 8) != 0))
         return CORR_EUNSUPPORTED;
@@ -378,32 +476,13 @@ corr_status corr_xengine(corr_t *c, const void *chan_in, const float *gains, voi
     const float2 *g = reinterpret_cast<const float2 *>(gains);
     corr_status s;
     cudaStream_t st = corr::as_stream(stream);
-    const bool fp16 = h.precision == CORR_PREC_FP16 || h.precision == CORR_PREC_FP16_HILO;
-    if (h.flags & CORR_FLAG_PLANAR) {
-        s = corr::launch_xengine_tma(h, chan_in, 2, g, store, st);
-    } else if (fp16 && (h.precision == CORR_PREC_FP16_HILO || h.xengine == CORR_XENG_AUTO) &&
-               corr::xengine_tma_supported(h)) {
-        // FP16 tensor-core path: one pass to planar FP16 operands, then the TMA X-engine
-        const int npl = h.precision == CORR_PREC_FP16_HILO ? 4 : 2;
-        const size_t need = (size_t)h.n_chan * npl * h.n_in * h.n_spectra * 2;
-        if (h.planar_ws_bytes < need) {
-            cudaFree(h.planar_ws);
-            h.planar_ws = nullptr;
-            h.planar_ws_bytes = 0;
-            if (cudaMalloc(&h.planar_ws, need) != cudaSuccess) {
-                cudaGetLastError();
-                return CORR_ENOMEM;
-            }
-            h.planar_ws_bytes = need;
-        }
-        s = corr::launch_to_planar(h, static_cast<const float2 *>(chan_in), h.planar_ws, npl, st);
-        if (s == CORR_OK) s = corr::launch_xengine_tma(h, h.planar_ws, npl, g, store, st);
-    } else if (h.precision == CORR_PREC_FP16_HILO || (h.flags & CORR_FLAG_FUSED_DUMP)) {
-        s = CORR_EUNSUPPORTED;  // the hi/lo products and the fused dump need the TMA path
-    } else if (corr::use_tc(h))
-        s = corr::launch_xengine_tc(h, chan_in, g, store, st);
-    else
+    if (corr::use_tc(h)) {
+        corr::TcOperands op;
+        s = corr::tc_operands(h, chan_in, st, op);
+        if (s == CORR_OK) s = corr::launch_xengine_tma(h, op.planes, op.npl, g, op.row_scale, op.kstride, store, st);
+    } else {
         s = corr::launch_xengine_cudacore(h, chan_in, g, store, st);
+    }
     if (s == CORR_OK) {
         h.acc_zero = false;
         h.acc_spectra += h.n_spectra;
@@ -420,30 +499,14 @@ corr_status corr_xengine_cross(corr_t *c, const void *chan_in, const float *gain
         return CORR_EINVAL;
     if (!corr::aligned16(chan_in) || (reinterpret_cast<uintptr_t>(vis_out) & 7u) != 0) return CORR_EINVAL;
     if (gains && h.precision == CORR_PREC_INT8) return CORR_EINVAL;
+    if (!corr::use_tc(h)) return CORR_EUNSUPPORTED;
     corr::DeviceGuard dg(h.device);
     cudaStream_t st = corr::as_stream(stream);
-    const float2 *g = reinterpret_cast<const float2 *>(gains);
-    if (h.precision == CORR_PREC_INT8) {
-        if (!(h.flags & CORR_FLAG_PLANAR)) return CORR_EUNSUPPORTED;
-        return corr::launch_xengine_tma_rect(h, chan_in, 2, nullptr, p0, n_p, q0, n_q, vis_out, st);
-    }
-    const bool fp16 = h.precision == CORR_PREC_FP16 || h.precision == CORR_PREC_FP16_HILO;
-    if (!fp16 || h.xengine != CORR_XENG_AUTO || !corr::xengine_tma_supported(h)) return CORR_EUNSUPPORTED;
-    const int npl = h.precision == CORR_PREC_FP16_HILO ? 4 : 2;
-    const size_t need = (size_t)h.n_chan * npl * h.n_in * h.n_spectra * 2;
-    if (h.planar_ws_bytes < need) {
-        cudaFree(h.planar_ws);
-        h.planar_ws = nullptr;
-        h.planar_ws_bytes = 0;
-        if (cudaMalloc(&h.planar_ws, need) != cudaSuccess) {
-            cudaGetLastError();
-            return CORR_ENOMEM;
-        }
-        h.planar_ws_bytes = need;
-    }
-    corr_status s = corr::launch_to_planar(h, static_cast<const float2 *>(chan_in), h.planar_ws, npl, st);
+    corr::TcOperands op;
+    corr_status s = corr::tc_operands(h, chan_in, st, op);
     if (s != CORR_OK) return s;
-    return corr::launch_xengine_tma_rect(h, h.planar_ws, npl, g, p0, n_p, q0, n_q, vis_out, st);
+    return corr::launch_xengine_tma_rect(h, op.planes, op.npl, reinterpret_cast<const float2 *>(gains), op.row_scale,
+                                         op.kstride, p0, n_p, q0, n_q, vis_out, st);
 }
 
 corr_status corr_get_accum(corr_t *c, void *out, void *stream) {
@@ -557,7 +620,8 @@ corr_status corr_fx_host(corr_t *c, const void *volt_host, const float *chan_sca
     const int cb = (h.n_chan + NC - 1) / NC;
     for (int k = 0; k < NC; ++k) {
         const int c0 = k * cb, c1 = std::min(h.n_chan, c0 + cb);
-        corr_status s = corr::launch_xengine_tma_range(h, h.fx_chan, 2, nullptr, store, c0, c1, st);
+        corr_status s = corr::launch_xengine_tma_range(h, h.fx_chan, 2, nullptr, nullptr, h.n_spectra, store, c0, c1,
+                                                       st);
         if (s == CORR_OK && !fused) s = corr::launch_dump_range(h, c0, c1, st);
         if (s != CORR_OK) return s;
         CORR_CUDA_TRY(cudaEventRecord(ev[1 + NB + k], st));
@@ -588,6 +652,54 @@ corr_status corr_check_status(corr_t *c, void *stream) {
         return (corr_status)v;
     }
     return CORR_OK;
+}
+
+corr_status corr_set_stage_timing(corr_t *c, int32_t on) {
+    if (!c) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (!h.clock) {
+        h.clock = new (std::nothrow) corr::StageClock();
+        if (!h.clock) return CORR_ENOMEM;
+    }
+    h.clock->on = on != 0;
+    return CORR_OK;
+}
+
+corr_status corr_stage_times(corr_t *c, double *ms, int64_t *launches) {
+    if (!c || !ms) return CORR_EINVAL;
+    Handle &h = c->h;
+    for (int k = 0; k < CORR_STAGE_COUNT; ++k) {
+        ms[k] = 0.0;
+        if (launches) launches[k] = 0;
+    }
+    if (!h.clock) return CORR_OK;
+    corr::DeviceGuard dg(h.device);
+    corr::StageClock &ck = *h.clock;
+    corr_status result = CORR_OK;
+    for (const corr::StageClock::Rec &r : ck.recs) {
+        float t = 0.f;
+        if (result == CORR_OK) {
+            cudaError_t e = cudaEventSynchronize(r.b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+            if (e != cudaSuccess) {
+                corr::set_cuda_error(e, "corr_stage_times");
+                result = CORR_ECUDA;
+            }
+        }
+        ms[r.stage] += (double)t;
+        ck.pool.push_back(r.a);
+        ck.pool.push_back(r.b);
+    }
+    ck.recs.clear();
+    if (launches)
+        for (int k = 0; k < CORR_STAGE_COUNT; ++k) launches[k] = ck.launches[k];
+    for (int64_t &n : ck.launches) n = 0;
+    if (result == CORR_OK && ck.overflow) {
+        corr::set_error_text("corr_stage_times: more than 65536 stage records since the last read");
+        result = CORR_ESTATE;
+    }
+    ck.overflow = false;
+    return result;
 }
 
 corr_status corr_reset(corr_t *c, void *stream) {

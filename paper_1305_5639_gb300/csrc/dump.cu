@@ -89,6 +89,7 @@ corr_status launch_dump_range(const Handle &h, int c0, int c1, cudaStream_t st) 
     const long long n = (long long)(c1 - c0) * h.n_base;
     if (n <= 0) return CORR_OK;
     const long long off = (long long)c0 * h.n_base;
+    StageScope sc(h, CORR_STAGE_DUMP, st);
     long long blocks = (n + 255) / 256;
     const long long cap = (long long)h.n_sm * 16;
     if (blocks > cap) blocks = cap;

@@ -30,6 +30,7 @@ FShape shape_of(const Handle &h) {
 // FP32 buffer, and the FFT pass then reads those (float input, phase only).
 corr_status pfb_front(const Handle &h, FShape &f, const void *&volt, cudaStream_t st) {
     if (!h.pfb_win) return CORR_OK;
+    StageScope sc(h, CORR_STAGE_PFB, st);
     const corr_status s = launch_pfb_fir(h, volt, f.i0, f.n_run < 0 ? f.n_in : f.n_run, st);
     if (s != CORR_OK) return s;
     volt = h.pfb_y;
@@ -65,6 +66,7 @@ corr_status launch_fengine_range(const Handle &h, const void *volt, const float 
     if (n_run == 0) return CORR_OK;
     corr_status s = pfb_front(h, f, volt, st);
     if (s != CORR_OK) return s;
+    StageScope sc(h, CORR_STAGE_FENGINE, st);
     if (h.precision == CORR_PREC_INT8 && (h.flags & CORR_FLAG_PLANAR))
         return dispatch<kRequantPlanar>(f, volt, scale, out, nullptr, st);
     if (h.precision == CORR_PREC_INT8) return dispatch<kRequant>(f, volt, scale, out, nullptr, st);
@@ -80,6 +82,7 @@ corr_status launch_fengine_power(const Handle &h, const void *volt, float *power
     FShape f = shape_of(h);
     corr_status s = pfb_front(h, f, volt, st);
     if (s != CORR_OK) return s;
+    StageScope sc(h, CORR_STAGE_POWER, st, 2);
     return power_pass(f, volt, h.power64, power, st);
 }
 

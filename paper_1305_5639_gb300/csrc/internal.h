@@ -4,9 +4,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "corr.h"
 
 namespace corr {
+
+// Optional per-stage timing of the kernels a handle launches (corr_set_stage_timing):
+// a pair of CUDA events around each stage's launches on the stream they run on.
+struct StageClock {
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;  // spare events (created on demand, kept for reuse)
+    std::vector<Rec> recs;          // recorded, not yet read
+    int64_t launches[CORR_STAGE_COUNT] = {};
+    bool on = false;
+    bool overflow = false;          // more records than kMaxRecs since the last read
+    static constexpr size_t kMaxRecs = 1 << 16;
+};
 
 // Handle state. Device buffers are owned by the library.
 struct Handle {
@@ -42,6 +59,23 @@ struct Handle {
     cudaEvent_t fx_ev[40] = {};
     bool fx_ready = false;  // every fx_* resource above was created
     size_t bwd_ws_bytes = 0;
+    StageClock *clock = nullptr;  // stage timing (null until first enabled)
+};
+
+// Records the stage's start event on construction and its end event on destruction
+// when the handle's stage timing is on; counts n_launch kernel launches either way.
+class StageScope {
+  public:
+    StageScope(const Handle &h, int stage, cudaStream_t st, int n_launch = 1);
+    ~StageScope();
+    StageScope(const StageScope &) = delete;
+    StageScope &operator=(const StageScope &) = delete;
+
+  private:
+    StageClock *c_;
+    int stage_;
+    cudaStream_t st_;
+    cudaEvent_t a_ = nullptr;
 };
 
 // Error bookkeeping (per thread).
@@ -79,14 +113,16 @@ corr_status launch_fengine(const Handle &h, const void *volt, const float *scale
 corr_status launch_fengine_power(const Handle &h, const void *volt, float *power, cudaStream_t st);
 corr_status launch_xengine_cudacore(const Handle &h, const void *chan_in, const float2 *gains,
                                     bool store, cudaStream_t st);
-corr_status launch_xengine_tc(const Handle &h, const void *chan_in, const float2 *gains, bool store,
-                              cudaStream_t st);
 corr_status launch_dump(const Handle &h, cudaStream_t st);
 corr_status launch_dump_range(const Handle &h, int c0, int c1, cudaStream_t st);
 corr_status launch_fengine_range(const Handle &h, const void *volt, const float *scale, void *out, int i0, int n_run,
                                  cudaStream_t st);
-corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
-                                     int c0, int c1, cudaStream_t st);
+// TMA X-engine over channels [c0, c1) of planar FP16 operands [chan][npl][n_in][kstride]
+// (kstride >= n_spectra, a multiple of 8); row_scale [chan][n_in] (or null): the
+// factors 2^-e of the FP16 paths' per-row range scaling, undone in the epilogue.
+corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int npl, const float2 *gains,
+                                     const float *row_scale, int kstride, bool store, int c0, int c1,
+                                     cudaStream_t st);
 size_t backward_workspace_bytes(const Handle &h);
 corr_status launch_backward_ws(const Handle &h, const float2 *grad_vis, const float2 *chan_in,
                                const float2 *gains, float2 *grad_chan, float2 *grad_gains, float2 *ws,
@@ -108,8 +144,9 @@ corr_status launch_adj_reduce(const float2 *part, double2 *scratch, float2 *dg, 
                               cudaStream_t st);
 // Cross-only rectangle of the visibility matrix on the TMA X-engine: inputs
 // [p0, p0 + n_p) x [q0, q0 + n_q), output [n_chan][n_p][n_q] overwritten.
-corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl, const float2 *gains, int p0,
-                                    int n_p, int q0, int n_q, void *out, cudaStream_t st);
+corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl, const float2 *gains,
+                                    const float *row_scale, int kstride, int p0, int n_p, int q0, int n_q, void *out,
+                                    cudaStream_t st);
 // Bounded-wait self-test (selftest.cu): CORR_OK if a wait that nothing completes gave up
 // after limit_ns, recorded CORR_ETIMEOUT and returned.
 corr_status selftest_bounded_wait(uint64_t limit_ns);
@@ -118,9 +155,18 @@ corr_status selftest_bounded_wait(uint64_t limit_ns);
 corr_status launch_pfb_fir(const Handle &h, const void *volt, int i0, int n_run, cudaStream_t st);
 bool fengine_supported(int n_chan);
 bool xengine_tma_supported(const Handle &h);
-corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
-                               cudaStream_t st);
-corr_status launch_to_planar(const Handle &h, const float2 *X, void *out, int npl, cudaStream_t st);
+corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains,
+                               const float *row_scale, int kstride, bool store, cudaStream_t st);
+// FP16 operand preparation (prep.cu): complex float [chan][n_in][K] -> planes
+// [chan][npl][n_in][planar_kstride(K)] with a per-row power-of-two range scale, whose
+// reciprocals planar_row_scale() points at, inside one workspace of planar_ws_bytes().
+int planar_kstride(int K);
+size_t planar_ws_bytes(const Handle &h, int npl);
+float *planar_row_scale(const Handle &h, void *ws, int npl);
+corr_status launch_to_planar(const Handle &h, const float2 *X, void *ws, int npl, cudaStream_t st);
+// Complex int8 [chan][n_in][K] -> planar FP16 codes [chan][2][n_in][planar_kstride(K)] (exact).
+corr_status launch_i8_to_planar(const Handle &h, const void *X, void *ws, cudaStream_t st);
+bool tma_available();
 
 // One sub-array of a batched X-engine launch (device-side descriptor).
 struct BatchSub {

@@ -209,6 +209,7 @@ corr_status launch_xengine_cudacore(const Handle &h, const void *chan_in, const 
                                     cudaStream_t st) {
     const int nb = (h.n_in + TB - 1) / TB;
     dim3 grid(nb * (nb + 1) / 2, h.n_chan);
+    StageScope sc(h, CORR_STAGE_XENGINE, st);
     if (h.precision == CORR_PREC_INT8) {
         k_xeng_i8<<<grid, NTH, 0, st>>>(static_cast<const char2 *>(chan_in), static_cast<int2 *>(h.acc), h.n_in,
                                         h.n_spectra, h.n_base, store ? 1 : 0);

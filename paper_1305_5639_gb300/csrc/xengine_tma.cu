@@ -96,6 +96,7 @@ struct TParams {
     int batch;
     int c0;  // first channel of a channel-range launch
     const float2 *gains;
+    const float *rsc;  // FP16: per-(channel, input) factors 2^-e of the operands' range scaling, or null
     int *status;
     long long B;
     long long n_items;
@@ -471,6 +472,10 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
             const int gi0 = p.rect ? p.p0 : 0, gj0 = p.rect ? p.q0 : 0;
             float2 gi = make_float2(1.f, 0.f);
             if (p.gains && i < (p.rect ? p.n_p : itm.n_in)) gi = __ldg(p.gains + gi0 + i);
+            // the operands' range scaling: V_ij carries 2^e_i 2^e_j, undone here (exact)
+            const float *rs = p.rsc ? p.rsc + (long long)chan * p.n_in : nullptr;
+            float si = 1.f;
+            if (rs && i < (p.rect ? p.n_p : itm.n_in)) si = __ldg(rs + gi0 + i);
 #pragma unroll 1
             for (int cb = 0; cb < 4; ++cb) {
                 // D1 = (re_I re_J | re_I im_J) in columns 0..255, D2 = (im_I re_J | im_I im_J) in 256..511
@@ -487,8 +492,12 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
                 for (int x = 0; x < 8; ++x) {
                     float2 v = make_float2(__uint_as_float(a1[x]) + __uint_as_float(b2[x]),
                                            __uint_as_float(a2[x]) - __uint_as_float(b1[x]));
+                    const int jg = min(jb + x, (p.rect ? p.n_q : itm.n_in) - 1);  // clamped: unused past the end
+                    if (rs) {
+                        const float sij = si * __ldg(rs + gj0 + jg);
+                        v = make_float2(v.x * sij, v.y * sij);
+                    }
                     if (p.gains) {
-                        const int jg = min(jb + x, (p.rect ? p.n_q : itm.n_in) - 1);  // clamped: unused past the end
                         const float2 gj = __ldg(p.gains + gj0 + jg);
                         const float2 w = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
                         v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
@@ -761,6 +770,8 @@ EncodeTiledFn encode_fn() {
 
 }  // namespace
 
+bool tma_available() { return encode_fn() != nullptr; }
+
 bool xengine_tma_supported(const Handle &h) { return (h.n_spectra % 8) == 0 && encode_fn() != nullptr; }
 
 corr_status tma_encode_planar(void *tmap128, const void *planes, int n_in, int n_chan, int K, int npl,
@@ -825,26 +836,28 @@ corr_status launch_xengine_tma_batch(const void *d_tmaps, const BatchSub *d_subs
     return check_launch("k_xeng_tma (batched)");
 }
 
-corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
-                               cudaStream_t st) {
-    return launch_xengine_tma_range(h, planes, npl, gains, store, 0, h.n_chan, st);
+corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains,
+                               const float *row_scale, int kstride, bool store, cudaStream_t st) {
+    return launch_xengine_tma_range(h, planes, npl, gains, row_scale, kstride, store, 0, h.n_chan, st);
 }
 
-corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int npl, const float2 *gains, bool store,
-                                     int c0, int c1, cudaStream_t st) {
+corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int npl, const float2 *gains,
+                                     const float *row_scale, int kstride, bool store, int c0, int c1,
+                                     cudaStream_t st) {
     if (c1 <= c0) return CORR_OK;
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
         set_error_text("cuTensorMapEncodeTiled is not available from the driver");
         return CORR_EUNSUPPORTED;
     }
-    if ((h.n_spectra % 8) != 0 || (npl != 2 && npl != 4)) return CORR_EUNSUPPORTED;
+    if ((kstride % 8) != 0 || kstride < h.n_spectra || (npl != 2 && npl != 4)) return CORR_EUNSUPPORTED;
     const int kb = npl == 2 ? 64 : 32;
-    // planar FP16 tensor: dims (innermost first) spectrum, input, plane, channel
+    // planar FP16 tensor: dims (innermost first) spectrum, input, plane, channel; rows of
+    // kstride elements (16-byte multiples), spectra past n_spectra read as zeros
     CUtensorMap tmap;
     const cuuint64_t dims[4] = {(cuuint64_t)h.n_spectra, (cuuint64_t)h.n_in, (cuuint64_t)npl, (cuuint64_t)h.n_chan};
-    const cuuint64_t strides[3] = {(cuuint64_t)h.n_spectra * 2, (cuuint64_t)h.n_spectra * 2 * h.n_in,
-                                   (cuuint64_t)h.n_spectra * 2 * h.n_in * npl};
+    const cuuint64_t strides[3] = {(cuuint64_t)kstride * 2, (cuuint64_t)kstride * 2 * h.n_in,
+                                   (cuuint64_t)kstride * 2 * h.n_in * npl};
     const cuuint32_t box[4] = {(cuuint32_t)kb, TILE, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(planes), dims, strides, box, estr,
@@ -858,6 +871,7 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
     p.acc = h.acc;
     p.vis64 = (h.flags & CORR_FLAG_FUSED_DUMP) ? h.vis64 : nullptr;
     p.gains = gains;
+    p.rsc = row_scale;
     p.status = h.status;
     p.B = h.n_base;
     const int nb = (h.n_in + TILE - 1) / TILE;
@@ -873,6 +887,7 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
         p.st_nchan = h.n_chan;
     }
     const unsigned grid = (unsigned)(p.n_items < h.n_sm ? p.n_items : h.n_sm);
+    StageScope sc(h, CORR_STAGE_XENGINE, st);
     if (h.precision == CORR_PREC_INT8 && p.st_out) {
         using C = TCfg<2, 64>;
         auto kern = k_xeng_tma<kInt8, C, true>;
@@ -888,20 +903,21 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
     return check_launch("k_xeng_tma");
 }
 
-corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl, const float2 *gains, int p0,
-                                    int n_p, int q0, int n_q, void *out, cudaStream_t st) {
+corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl, const float2 *gains,
+                                    const float *row_scale, int kstride, int p0, int n_p, int q0, int n_q, void *out,
+                                    cudaStream_t st) {
     if (n_p <= 0 || n_q <= 0) return CORR_OK;
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
         set_error_text("cuTensorMapEncodeTiled is not available from the driver");
         return CORR_EUNSUPPORTED;
     }
-    if ((h.n_spectra % 8) != 0 || (npl != 2 && npl != 4)) return CORR_EUNSUPPORTED;
+    if ((kstride % 8) != 0 || kstride < h.n_spectra || (npl != 2 && npl != 4)) return CORR_EUNSUPPORTED;
     const int kb = npl == 2 ? 64 : 32;
     CUtensorMap tmap;
     const cuuint64_t dims[4] = {(cuuint64_t)h.n_spectra, (cuuint64_t)h.n_in, (cuuint64_t)npl, (cuuint64_t)h.n_chan};
-    const cuuint64_t strides[3] = {(cuuint64_t)h.n_spectra * 2, (cuuint64_t)h.n_spectra * 2 * h.n_in,
-                                   (cuuint64_t)h.n_spectra * 2 * h.n_in * npl};
+    const cuuint64_t strides[3] = {(cuuint64_t)kstride * 2, (cuuint64_t)kstride * 2 * h.n_in,
+                                   (cuuint64_t)kstride * 2 * h.n_in * npl};
     const cuuint32_t box[4] = {(cuuint32_t)kb, TILE, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(planes), dims, strides, box, estr,
@@ -913,6 +929,7 @@ corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl
     }
     TParams p{};
     p.gains = gains;
+    p.rsc = row_scale;
     p.status = h.status;
     p.B = h.n_base;
     p.rect = 1;
@@ -929,6 +946,7 @@ corr_status launch_xengine_tma_rect(const Handle &h, const void *planes, int npl
     p.K = h.n_spectra;
     p.store = 1;
     const unsigned grid = (unsigned)(p.n_items < h.n_sm ? p.n_items : h.n_sm);
+    StageScope sc(h, CORR_STAGE_XENGINE, st);
     if (h.precision == CORR_PREC_INT8) {
         const corr_status s = launch_int8_wide(tmap, p, grid, st);
         if (s != CORR_OK) return s;
@@ -993,6 +1011,7 @@ corr_status launch_adjoint_tma(const Handle &h, const void *a_planes, const void
     p.part = part;
     p.expo = expo;
     const unsigned grid = (unsigned)(p.n_items < h.n_sm ? p.n_items : h.n_sm);
+    StageScope sc(h, CORR_STAGE_ADJ_GEMM, st);
     CORR_CUDA_TRY(cudaFuncSetAttribute(k_xeng_tma<kAdj, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
     k_xeng_tma<kAdj, C><<<grid, NTHREADS, C::SMEM_BYTES, st>>>(ta, tb, p);
     return check_launch("k_xeng_tma (adjoint)");

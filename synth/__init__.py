@@ -104,10 +104,12 @@ def delays_int8(n_ant: int, seed: int = 0, max_delay: int = 15) -> np.ndarray:
 
 
 def volt_int8(n_ant: int, n_pol: int, n_chan: int, n_spectra: int, seed: int = 0, sigma: float = 16.0,
-              src_sigma: float = 1.6, max_delay: int = 15) -> np.ndarray:
+              src_sigma: float = 1.6, max_delay: int = 15, lo: int = -127) -> np.ndarray:
     """Raw complex int8 voltages [n_in, n_spectra * n_chan, 2] (input i = ant * n_pol
-    + pol): Re, Im = clip(rint(sigma z + src[t - d_ant]), -127, 127), src Re/Im iid
-    N(0, src_sigma^2), d_ant uniform on {0..max_delay} shared by both pols."""
+    + pol): Re, Im = clip(rint(sigma z + src[t - d_ant]), lo, 127), src Re/Im iid
+    N(0, src_sigma^2), d_ant uniform on {0..max_delay} shared by both pols. The
+    workloads clip symmetrically (lo = -127); lo = -128 lets the edge tests reach
+    the one int8 code whose negation is not an int8."""
     N, K = n_chan, n_spectra
     n_in = n_ant * n_pol
     d = delays_int8(n_ant, seed, max_delay)
@@ -120,7 +122,7 @@ def volt_int8(n_ant: int, n_pol: int, n_chan: int, n_spectra: int, seed: int = 0
         z = _normal_pair(_rng(seed, _T_NOISE, i), T, sigma)
         z += src[max_delay - int(d[a]): max_delay - int(d[a]) + T]
         np.rint(z, out=z)
-        np.clip(z, -127.0, 127.0, out=z)
+        np.clip(z, float(lo), 127.0, out=z)
         out[i] = z.astype(np.int8)
 
     with _pool() as ex:
@@ -134,16 +136,17 @@ def _chan_list(n_chan: int, chans):
 
 
 def chan_int8(n_chan: int, n_in: int, n_spectra: int, seed: int = 0, chans=None,
-              sigma: float = 16.0) -> np.ndarray:
+              sigma: float = 16.0, lo: int = -127) -> np.ndarray:
     """Channelised complex int8 [n_sel, n_in, n_spectra, 2]: Re, Im =
-    clip(rint(sigma z), -127, 127), one stream per channel."""
+    clip(rint(sigma z), lo, 127), one stream per channel (lo = -128 for the edge
+    tests; the workloads use -127)."""
     cl = _chan_list(n_chan, chans)
     out = np.empty((len(cl), n_in, n_spectra, 2), dtype=np.int8)
 
     def fill(t):
         z = _normal_pair(_rng(seed, _T_CHAN, cl[t]), n_in * n_spectra, sigma)
         np.rint(z, out=z)
-        np.clip(z, -127.0, 127.0, out=z)
+        np.clip(z, float(lo), 127.0, out=z)
         out[t] = z.reshape(n_in, n_spectra, 2).astype(np.int8)
 
     with _pool() as ex:

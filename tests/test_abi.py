@@ -66,7 +66,9 @@ def test_create_rejects_bad_arguments_without_device(lib):
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
     o = corr_opts(1, 0, 1, -1)  # ... and needs n_spectra % 8 == 0
     assert lib.corr_create(4, 1, 16, 12, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
-    o = corr_opts(1, 0, 2, -1)  # the fused dump needs the planar X-engine
+    o = corr_opts(1, 1, 2, -1)  # the fused dump needs the tensor-core X-engine
+    assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
+    o = corr_opts(0, 2, 0, -1)  # FP32 has no tensor-core X-engine
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED
     # INT8 guard: n_spectra * 2 * 128^2 must stay below 2^31 (int8 codes include -128;
     # 65536 spectra is the first to fail)
@@ -89,6 +91,8 @@ def test_null_handle_calls(lib):
     assert lib.corr_dump(None, None, None) == CORR_EINVAL
     assert lib.corr_backward(None, None, None, None, None, None, None) == CORR_EINVAL
     assert lib.corr_n_baselines(None) == -1
+    assert lib.corr_set_stage_timing(None, 1) == CORR_EINVAL
+    assert lib.corr_stage_times(None, None, None) == CORR_EINVAL
 
 
 def test_int8_guard_boundary_is_exact():

@@ -29,6 +29,27 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def _elem(a, b):
+    """Element-wise error: max |a - b| over each channel's entries (first axis),
+    divided by that channel's rms of b; the largest over the channels. A wrong
+    row, tile edge or channel exponent shows up here at O(1) even where it hides
+    inside a global norm."""
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    rms = np.sqrt(np.mean(np.abs(b) ** 2, axis=1))
+    return float(np.max(np.max(np.abs(a - b), axis=1) / rms))
+
+
+def _elem_dg(a, b):
+    """max_m |dg_m - ref_m| / rms(ref)."""
+    return float(np.max(np.abs(a - b)) / np.sqrt(np.mean(np.abs(b) ** 2)))
+
+
+# element-wise bars: ten times the 1e-4 relative-L2 gradient bar, room for the
+# extreme-value tail of up to ~5e8 entries (the calibration workload)
+ELEM = 1e-3
+
+
 @pytest.mark.parametrize("n_in,K,n_chan,auto_w", [(64, 64, 2, 0.0), (136, 200, 3, 1.0), (520, 264, 2, 0.0),
                                                   (8, 8, 1, 1.0)])
 def test_backward_tc_matches_oracle_gradient(cuda_ok, n_in, K, n_chan, auto_w):
@@ -38,6 +59,8 @@ def test_backward_tc_matches_oracle_gradient(cuda_ok, n_in, K, n_chan, auto_w):
     c.check_status()
     assert _rel(dX.cpu().numpy(), dX_ref) <= 1e-4
     assert _rel(dg.cpu().numpy(), dg_ref) <= 1e-4
+    assert _elem(dX.cpu().numpy(), dX_ref) <= ELEM
+    assert _elem_dg(dg.cpu().numpy(), dg_ref) <= ELEM
     c.close()
 
 
@@ -53,6 +76,8 @@ def test_backward_tc_gradient_scale_invariant(cuda_ok, scale):
     c.check_status()
     assert _rel(dX.cpu().numpy(), dX_ref * scale) <= 1e-4
     assert _rel(dg.cpu().numpy(), dg_ref * scale) <= 1e-4
+    assert _elem(dX.cpu().numpy(), dX_ref * scale) <= ELEM
+    assert _elem_dg(dg.cpu().numpy(), dg_ref * scale) <= ELEM
     c.close()
 
 
@@ -69,6 +94,8 @@ def test_backward_tc_partial_outputs(cuda_ok):
     assert torch.equal(dX_only, dX_both)
     assert torch.equal(dg_only, dg_both)
     assert _rel(dX_both.cpu().numpy(), dX_ref) <= 1e-4
+    assert _elem(dX_both.cpu().numpy(), dX_ref) <= ELEM
+    assert _elem_dg(dg_both.cpu().numpy(), dg_ref) <= ELEM
     c.close()
 
 
@@ -83,6 +110,7 @@ def test_backward_tc_unit_gains(cuda_ok):
     c.check_status()
     assert _rel(dX.cpu().numpy(), ref_dX.cpu().numpy()) <= 1e-4
     assert _rel(dg.cpu().numpy(), ref_dg.cpu().numpy()) <= 1e-4
+    assert _elem(dX.cpu().numpy(), ref_dX.cpu().numpy()) <= ELEM
     c.close()
     c32.close()
 

@@ -65,3 +65,28 @@ def test_bounded_wait_selftest_times_out_and_context_survives(cuda_ok):
     c.check_status()
     assert np.array_equal(c.accum().cpu().numpy().astype(np.int64), oracle.cmac(X))
     c.close()
+
+
+def test_stage_timing_counts_and_times_each_stage(cuda_ok):
+    """Per-stage event timing (tracing): an FP16 hi/lo step records the operand
+    conversion, the X-engine and the dump separately, one launch each, with
+    positive times; reading clears; switched off, launches are still counted but
+    not timed."""
+    n_in, K, n_chan = 130, 96, 3
+    X = torch.from_numpy(synth.chan_sources(n_chan, n_in, K, n_src=2, seed=4, src_amp=0.1)).to(DEV)
+    c = api.Correlator(n_in, 1, n_chan, K, precision="fp16_hilo")
+    c.set_stage_timing(True)
+    for _ in range(2):
+        c.xengine(X)
+        c.dump(copy=False)
+    t = c.stage_times()
+    for st in ("prep", "xengine", "dump"):
+        assert t[st][1] == 2 and t[st][0] > 0.0, (st, t[st])
+    assert t["fengine"] == (0.0, 0)
+    assert all(v == (0.0, 0) for v in c.stage_times().values())  # cleared by the read
+    c.set_stage_timing(False)
+    c.xengine(X)
+    t = c.stage_times()
+    assert t["xengine"] == (0.0, 1) and t["prep"] == (0.0, 1)
+    c.check_status()
+    c.close()

@@ -71,7 +71,8 @@ def test_cross_validation(cuda_ok):
             c.xengine_cross(X, *args)
         assert e.value.status == CORR_EINVAL, args
     c.close()
-    for kw in (dict(precision="int8"), dict(precision="fp32")):
+    # the rectangle runs on the tensor-core X-engine only
+    for kw in (dict(precision="int8", xengine="cudacore"), dict(precision="fp32")):
         c = api.Correlator(n_in, 1, 1, K, **kw)
         with pytest.raises(CorrError) as e:
             c.xengine_cross(torch.zeros((1, n_in, K, 2), dtype=torch.int8, device=DEV), 0, 8, 8, 8)

@@ -95,4 +95,10 @@ def test_adjoint_workload_full_launch(cuda_ok, precision):
     dg = dg.cpu().numpy()
     assert np.linalg.norm(dX - dX_ref) <= 1e-4 * np.linalg.norm(dX_ref)
     assert np.linalg.norm(dg - dg_ref) <= 1e-4 * np.linalg.norm(dg_ref)
+    # element-wise, per channel (a wrong row, tile edge or channel block would show
+    # at O(1)): max error over the channel's rms, ten times the L2 bar
+    rms = np.sqrt(np.mean(np.abs(dX_ref) ** 2, axis=(1, 2)))
+    e = np.max(np.abs(dX - dX_ref), axis=(1, 2)) / rms
+    assert np.max(e) <= 1e-3, (int(np.argmax(e)), float(np.max(e)))
+    assert np.max(np.abs(dg - dg_ref)) <= 1e-3 * np.sqrt(np.mean(np.abs(dg_ref) ** 2))
     c.close()

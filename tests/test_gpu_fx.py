@@ -203,6 +203,10 @@ def test_backward_matches_oracle_gradient(cuda_ok, n_in, K, n_chan, auto_w):
     dg = dg.cpu().numpy()
     assert np.linalg.norm(dX - dX_ref) <= 1e-4 * np.linalg.norm(dX_ref)
     assert np.linalg.norm(dg - dg_ref) <= 1e-4 * np.linalg.norm(dg_ref)
+    # element-wise, per channel: max error over the channel's rms (10x the L2 bar)
+    rms = np.sqrt(np.mean(np.abs(dX_ref) ** 2, axis=(1, 2)))
+    assert np.max(np.max(np.abs(dX - dX_ref), axis=(1, 2)) / rms) <= 1e-3
+    assert np.max(np.abs(dg - dg_ref)) <= 1e-3 * np.sqrt(np.mean(np.abs(dg_ref) ** 2))
     c.close()
 
 

@@ -227,7 +227,7 @@ def test_tma_fp16_paths(cuda_ok, prec, tol, n_in, K, n_chan):
     c.close()
 
 
-def test_tma_fp16_hilo_gains_and_converter_fp16(cuda_ok):
+def test_tma_fp16_hilo_gains_and_explicit_tcgen05(cuda_ok):
     n_in, K, n_chan = 140, 128, 2
     X = synth.chan_sources(n_chan, n_in, K, n_src=3, seed=8, src_amp=0.1)
     g = synth.gains(n_in, seed=8)
@@ -269,15 +269,42 @@ def test_tma_fp16_fused_dump_equals_separate_dump(cuda_ok, prec, with_gains):
 
 
 def test_fused_dump_flag_validation(cuda_ok):
+    """The fused dump lives in the tensor-core X-engine's epilogue: FP32 and the
+    CUDA-core X-engines refuse it."""
     from paper_1305_5639_gb300._lib import CorrError, CORR_EUNSUPPORTED
 
-    for kw in (dict(precision="fp32"), dict(precision="int8"), dict(precision="fp16", xengine="tcgen05")):
+    for kw in (dict(precision="fp32"), dict(precision="int8", xengine="cudacore"),
+               dict(precision="fp32", xengine="tcgen05")):
         with pytest.raises(CorrError) as e:
             api.Correlator(16, 1, 2, 64, fused_dump=True, **kw)
         assert e.value.status == CORR_EUNSUPPORTED, kw
-    with pytest.raises(CorrError) as e:  # FP16 fused needs n_spectra % 8 == 0
-        api.Correlator(16, 1, 2, 60, precision="fp16", fused_dump=True)
-    assert e.value.status == CORR_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("prec,K", [("int8", 100), ("fp16", 60), ("fp16_hilo", 37)])
+def test_fused_dump_any_layout_and_ragged_spectra(cuda_ok, prec, K):
+    """Complex int8 and complex float inputs (converted to planar operands by the
+    library, spectra padded to a multiple of 8) with the dump fused: equal to the
+    separate dump over two integrations."""
+    n_in, n_chan = 150, 2
+    if prec == "int8":
+        parts = [synth.chan_int8(n_chan, n_in, K, seed=90 + t) for t in range(2)]
+    else:
+        parts = [synth.chan_sources(n_chan, n_in, K, n_src=3, seed=90 + t, src_amp=0.1) for t in range(2)]
+    sep = api.Correlator(n_in, 1, n_chan, K, precision=prec)
+    fus = api.Correlator(n_in, 1, n_chan, K, precision=prec, fused_dump=True)
+    for X in parts:
+        Xt = torch.from_numpy(X).to(DEV)
+        sep.xengine(Xt)
+        sep.dump(copy=False)
+        fus.xengine(Xt)
+    a, b = sep.dump().cpu().numpy(), fus.dump().cpu().numpy()
+    fus.check_status()
+    assert np.array_equal(a, b)
+    if prec == "int8":
+        want = oracle.dump([oracle.cmac(X) for X in parts])
+        assert np.array_equal(a, want[..., 0] + 1j * want[..., 1])
+    sep.close()
+    fus.close()
 
 
 def test_fp16_workload_channel_two_integrations(cuda_ok):
@@ -353,3 +380,66 @@ def test_fx_host_back_to_back_calls(cuda_ok):
     c.check_status()
     c.close()
     ref.close()
+
+
+# --------------------------------------------------------------------------- FP16 range: any magnitude
+@pytest.mark.parametrize("prec,tol", [("fp16", 2e-3), ("fp16_hilo", 5e-5)])
+@pytest.mark.parametrize("mag", [1e-3, 1e3, 1e-6, 1e12])
+def test_fp16_paths_hold_their_bound_at_any_magnitude(cuda_ok, prec, tol, mag):
+    """The same N(0,1) + sources data scaled by 1e-3, 1e3, 1e-6 and 1e12: without
+    range scaling FP16 would round small values into its subnormals (losing the
+    hi/lo split's low part) and overflow large ones (above 65504). The per-row
+    power-of-two scaling keeps both bounds for any magnitude."""
+    n_in, K, n_chan = 200, 264, 2
+    X = synth.chan_sources(n_chan, n_in, K, n_src=3, seed=17, src_amp=0.1)
+    Xs = (X.astype(np.complex128) * mag).astype(np.complex64)
+    c = api.Correlator(n_in, 1, n_chan, K, precision=prec)
+    c.xengine(torch.from_numpy(Xs).to(DEV))
+    V = c.accum().cpu().numpy().astype(np.complex128)
+    c.check_status()
+    assert np.all(np.isfinite(V))
+    emax, erms = norm_err(V, oracle.cmac(Xs), n_in)
+    assert emax <= tol, (prec, mag, emax, erms)
+    c.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16", 2e-3), ("fp16_hilo", 5e-5)])
+def test_fp16_paths_inputs_of_very_different_magnitudes(cuda_ok, prec, tol):
+    """Inputs spanning twelve decades within one channel (input i scaled by
+    10^((i mod 13) - 6)), with gains, K not a multiple of 8, and the cross-only
+    rectangle: each row gets its own power of two, so every normalised error
+    e_ij = |dV_ij| / sqrt(|V_ii| |V_jj|) stays within the bound."""
+    n_in, K, n_chan = 150, 93, 2
+    X = synth.chan_sources(n_chan, n_in, K, n_src=3, seed=23, src_amp=0.1).astype(np.complex128)
+    X *= (10.0 ** ((np.arange(n_in) % 13) - 6))[None, :, None]
+    X = X.astype(np.complex64)
+    g = synth.gains(n_in, seed=23)
+    ref = oracle.apply_gains(oracle.cmac(X), g, n_in)
+    c = api.Correlator(n_in, 1, n_chan, K, precision=prec)
+    Xt, gt = torch.from_numpy(X).to(DEV), torch.from_numpy(g).to(DEV)
+    c.xengine(Xt, gt)
+    V = c.accum().cpu().numpy().astype(np.complex128)
+    c.check_status()
+    emax, erms = norm_err(V, ref, n_in)
+    assert emax <= tol, (prec, emax, erms)
+    p0, n_p, q0, n_q = 20, 70, 90, 60
+    out = c.xengine_cross(Xt, p0, n_p, q0, n_q, gains=gt).cpu().numpy().astype(np.complex128)
+    full = oracle.unpack_full(ref, n_in)
+    d = np.abs(np.diagonal(full, axis1=1, axis2=2))
+    norm = np.sqrt(d[:, p0:p0 + n_p, None] * d[:, None, q0:q0 + n_q])
+    assert np.max(np.abs(out - full[:, p0:p0 + n_p, q0:q0 + n_q]) / norm) <= tol
+    c.close()
+
+
+def test_int8_layout_cross_only(cuda_ok):
+    """The cross-only rectangle also takes complex int8 channelised data (converted
+    to planar codes by the library), bit-exact."""
+    n_in, K, n_chan = 140, 72, 2
+    X = synth.chan_int8(n_chan, n_in, K, seed=31)
+    c = api.Correlator(n_in, 1, n_chan, K, precision="int8")
+    out = c.xengine_cross(torch.from_numpy(X).to(DEV), 10, 120, 0, 140).cpu().numpy().astype(np.int64)
+    Vp = oracle.cmac(X)
+    full = oracle.unpack_full(Vp[..., 0] + 1j * Vp[..., 1], n_in)[:, 10:130, 0:140]
+    assert np.array_equal(out[..., 0], full.real.astype(np.int64))
+    assert np.array_equal(out[..., 1], full.imag.astype(np.int64))
+    c.close()
