@@ -104,8 +104,8 @@ typedef struct corr_opts {
  * FFT length and the A spectra of one accumulation; the handle itself, its
  * precisions and flags have no counterpart in the paper). opts may be NULL
  * (FP32, AUTO, current device). n_ant * n_pol <= 65535 (CORR_EINVAL otherwise).
- * The F-engine supports n_chan in {16, 64, 256, 1024}; the X-engine any
- * n_chan >= 1. For INT8, n_spectra * 2 * 128^2 must stay below 2^31
+ * The F-engine supports n_chan in {16, 64, 128, 256, 512, 1024, 2048, 4096}; the
+ * X-engine any n_chan >= 1. For INT8, n_spectra * 2 * 128^2 must stay below 2^31
  * (int8 codes include -128; CORR_EOVERFLOW otherwise). *out receives the handle
  * (NULL on error). */
 CORR_API corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_spectra,

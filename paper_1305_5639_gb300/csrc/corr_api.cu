@@ -300,16 +300,15 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
     ok = cudaMemset(h.acc, 0, acc_bytes) == cudaSuccess && cudaMemset(h.vis64, 0, nvis * sizeof(double2)) == cudaSuccess &&
          cudaMemset(h.status, 0, sizeof(int32_t)) == cudaSuccess;
     if (ok && h.twiddle) {
-        // F-engine twiddles W_N^(t k1) = exp(-j 2 pi t k1 / N) for the N = T x T split,
-        // laid out [k1][t]; computed in double, rounded once to float
-        int T = 1;
-        while (T * T < n_chan) T *= 2;
+        // F-engine twiddles W_N^(t k1) = exp(-j 2 pi t k1 / N) for the N = T1 x T2 split,
+        // laid out [k1][t] (k1 < T1, t < T2); computed in double, rounded once to float
+        const int T2 = corr::fengine_t2(n_chan), T1 = n_chan / T2;
         std::vector<float2> tw((size_t)n_chan);
-        for (int k1 = 0; k1 < T; ++k1) {
-            for (int t = 0; t < T; ++t) {
+        for (int k1 = 0; k1 < T1; ++k1) {
+            for (int t = 0; t < T2; ++t) {
                 const int m = (t * k1) % n_chan;
                 const double ang = 2.0 * M_PI * (double)m / (double)n_chan;
-                tw[(size_t)k1 * T + t] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+                tw[(size_t)k1 * T2 + t] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
             }
         }
         ok = cudaMemcpy(h.twiddle, tw.data(), sizeof(float2) * (size_t)n_chan, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -339,10 +338,9 @@ corr_status corr_set_delays(corr_t *c, const float *delays) {
         return CORR_OK;
     }
     const int N = h.n_chan;
-    int T = 1;
-    while (T * T < N) T *= 2;
+    const int T2 = corr::fengine_t2(N), T1 = N / T2;
     std::vector<int32_t> D((size_t)h.n_in);
-    std::vector<float2> ph((size_t)h.n_in * 2 * T);
+    std::vector<float2> ph((size_t)h.n_in * (T1 + T2));
     for (int i = 0; i < h.n_in; ++i) {
         const double t = (double)delays[i];
         if (!std::isfinite(t) || std::fabs(t) > 1.0e9) return CORR_EINVAL;
@@ -350,11 +348,14 @@ corr_status corr_set_delays(corr_t *c, const float *delays) {
         const double d = t >= 0 ? std::floor(t + 0.5) : -std::floor(-t + 0.5);
         const double f = t - d;
         D[(size_t)i] = (int32_t)d;
-        for (int k = 0; k < T; ++k) {
-            const double a1 = 2.0 * M_PI * (double)k * f / (double)N;
-            const double a2 = 2.0 * M_PI * (double)T * (double)k * f / (double)N;
-            ph[(size_t)i * 2 * T + k] = make_float2((float)std::cos(a1), (float)std::sin(a1));
-            ph[(size_t)i * 2 * T + T + k] = make_float2((float)std::cos(a2), (float)std::sin(a2));
+        // channel k = k1 + T1 k2: exp(+j 2 pi k f / N) = c[k1] d[k2]
+        for (int k1 = 0; k1 < T1; ++k1) {
+            const double a1 = 2.0 * M_PI * (double)k1 * f / (double)N;
+            ph[(size_t)i * (T1 + T2) + k1] = make_float2((float)std::cos(a1), (float)std::sin(a1));
+        }
+        for (int k2 = 0; k2 < T2; ++k2) {
+            const double a2 = 2.0 * M_PI * (double)T1 * (double)k2 * f / (double)N;
+            ph[(size_t)i * (T1 + T2) + T1 + k2] = make_float2((float)std::cos(a2), (float)std::sin(a2));
         }
     }
     if (!h.dly_int) {

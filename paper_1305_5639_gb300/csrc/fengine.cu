@@ -56,7 +56,7 @@ corr_status power_pass(const FShape &f, const void *volt, double *acc64, float *
 
 }  // namespace
 
-bool fengine_supported(int n) { return n == 16 || n == 64 || n == 256 || n == 1024; }
+bool fengine_supported(int n) { return fengine_t2(n) > 0; }
 
 corr_status launch_fengine_range(const Handle &h, const void *volt, const float *scale, void *out, int i0, int n_run,
                                  cudaStream_t st) {

@@ -2,14 +2,17 @@
 // Section 2), 8-bit re-packing of the spectra and corner turn to channel-major
 // order, in one pass.
 //
-// Each N = T x T point FFT is computed by T threads in two register passes
-// (four-step / Cooley-Tukey split n = t + T m, k = k1 + T k2):
-//   pass 1: thread t holds x[t + T m], m < T, and computes the T-point DFT over m;
-//           the result is multiplied by W_N^(t k1) (twiddle table copied to shared
-//           memory per CTA)
+// Each N = T1 x T2 point FFT is computed by a group of max(T1, T2) threads in two
+// register passes (four-step / Cooley-Tukey split n = t + T2 m, k = k1 + T1 k2):
+//   pass 1: thread t < T2 holds x[t + T2 m], m < T1, and computes the T1-point DFT
+//           over m; the result is multiplied by W_N^(t k1) (twiddle table copied
+//           to shared memory per CTA)
 //   exchange through shared memory (padded rows, conflict-free)
-//   pass 2: thread k1 holds Y[t][k1], t < T, and computes the T-point DFT over t,
-//           giving X[k1 + T k2].
+//   pass 2: thread k1 < T1 holds Y[t][k1], t < T2, and computes the T2-point DFT
+//           over t, giving X[k1 + T1 k2].
+// Square lengths (16, 64, 256, 1024) keep every thread busy in both passes; the
+// others (128, 512, 2048, 4096: T2 = 2 T1 or T1 = T2 = 64) leave the threads past
+// the shorter dimension idle in one pass.
 // A CTA handles one input and SB consecutive spectra; the outputs are staged in
 // shared memory as [channel][spectrum] so that every (channel, input) row segment
 // of SB spectra is written to global memory contiguously (the corner turn). Raw
@@ -37,10 +40,10 @@ namespace corr {
 struct FShape {
     int n_in, n_chan, n_spectra;
     bool i8;
-    const float2 *tw;  // [k1][t] table for n_chan = T x T
+    const float2 *tw;  // [k1][t] table for n_chan = T1 x T2
     int i0 = 0, n_run = -1;  // inputs [i0, i0 + n_run) of the n_in (n_run < 0: all)
     const int *dint = nullptr;     // per-input integer advance (delay compensation), or null
-    const float2 *dph = nullptr;   // per-input phase tables [n_in][2 T]: c[k1], then d[k2]
+    const float2 *dph = nullptr;   // per-input phase tables [n_in][T1 + T2]: c[k1], then d[k2]
 };
 
 namespace {
@@ -48,40 +51,43 @@ namespace {
 
 constexpr int kThreads = 256;
 
-constexpr int isqrt_pow4(int n) { return n <= 1 ? 1 : 2 * isqrt_pow4(n / 4); }
-
 enum Mode { kFloatOut = 0, kRequant = 1, kPower = 2, kRequantPlanar = 3 };
 
 template <int N, bool I8, int MODE>
 struct FCfg {
-    static constexpr int T = isqrt_pow4(N);
-    static_assert(T * T == N, "N must be a power of 4");
-    static constexpr int G = kThreads / T;  // FFTs in flight per CTA
-    // Exchange buffer of one FFT: T rows of EXS floats; row k1 receives Y[0..T-1][k1]
+    static constexpr int T2 = fengine_t2(N);  // pass-1 threads = pass-2 DFT length
+    static constexpr int T1 = N / T2;         // pass-1 DFT length = pass-2 threads
+    static_assert(T2 > 0 && T1 * T2 == N && T1 <= T2 && T2 <= 64, "unsupported F-engine length");
+    static constexpr int TG = T2;             // threads per FFT group
+    static constexpr int G = kThreads / TG;   // FFTs in flight per CTA
+    // Exchange buffer of one FFT: T1 rows of EXS floats; row k1 receives Y[0..T2-1][k1]
     // (one column per writing thread) and is read back as float4. EXS and the per-FFT
     // stride GS keep both the scalar writes and the float4 reads free of bank conflicts:
-    // 4 EXS / 4 odd per quarter warp, and GS = T (mod 32) so that the FFTs sharing a
+    // 4 EXS / 4 odd per quarter warp, and GS = TG (mod 32) so that the FFTs sharing a
     // warp write to disjoint banks.
-    static constexpr int EXS = T == 4 ? 8 : T + 4;
-    static constexpr int GS = T * EXS + (T == 32 ? 0 : T);
+    static constexpr int EXS = T2 == 4 ? 8 : T2 + 4;
+    static constexpr int GS = T1 * EXS + (TG >= 32 ? 0 : TG);
     static constexpr bool RQ = MODE == kRequant || MODE == kRequantPlanar;
-    // spectra per CTA: the re-packing modes take 32 (64-byte row segments of the
-    // planar FP16 planes, 2 CTAs/SM at N = 1024)
-    static constexpr int SB = MODE == kFloatOut ? 8 : (RQ ? 32 : 16);
-    static_assert(SB % (G < SB ? G : SB) == 0 || G >= SB, "");
+    // spectra per CTA: the re-packing modes take 32 up to N = 1024 (64-byte row
+    // segments of the planar FP16 planes, 2 CTAs/SM at N = 1024), fewer for longer
+    // transforms so that the staging rows stay at 64 KB
+    static constexpr int SB = MODE == kFloatOut ? (N <= 1024 ? 8 : 8192 / N) : (RQ ? (N <= 1024 ? 32 : 32768 / N) : 16);
     // staging row stride in 32-bit words. The re-packing modes stage one 16-bit code
-    // pair per (channel k, spectrum s): a row of SB / 2 = 16 words whose word index is
-    // XOR-swizzled with (k >> 1) & 15, so that the 16-bit writes of one warp (32
-    // consecutive rows) and the 4-word row reads of the copy-out are free of bank
-    // conflicts. The FP32 mode stages float2 values in padded rows.
+    // pair per (channel k, spectrum s): a row of SB / 2 words whose word index is
+    // XOR-swizzled with (k >> SW) & (ROWW - 1), SW = log2(32 / ROWW), so that the
+    // 16-bit writes of one warp (32 consecutive rows) and the 4-word row reads of the
+    // copy-out are free of bank conflicts. The FP32 mode stages float2 values in
+    // padded rows.
     static constexpr int ROWW = RQ ? SB / 2 : (MODE == kFloatOut ? 2 * SB + 2 : 0);
-    static_assert(!RQ || ROWW == 16, "swizzle assumes 16-word rows");
+    static constexpr int SW = RQ ? ilog2(32 / ROWW) : 0;
+    static_assert(!RQ || (ROWW >= 4 && ROWW <= 16), "swizzle assumes 4..16-word rows");
     static constexpr size_t ex_bytes = sizeof(float) * (size_t)G * GS;
     static constexpr size_t pw_bytes = MODE == kPower ? sizeof(float) * N : 0;
     static constexpr size_t tw_bytes = sizeof(float2) * (size_t)N;  // twiddle table copy
-    static constexpr size_t dl_bytes = sizeof(float2) * 32;         // delay phases d[k2] (T <= 32)
+    static constexpr size_t dl_bytes = sizeof(float2) * 64;         // delay phases d[k2] (T2 <= 64)
     static constexpr size_t st_bytes = sizeof(uint32_t) * (size_t)N * ROWW;
     static constexpr size_t smem = ex_bytes + pw_bytes + tw_bytes + dl_bytes + st_bytes;
+    static_assert(smem <= 232448, "shared memory");
 };
 
 // 1.5 * 2^23: adding it to |v| <= 2^22 rounds v to the nearest integer (ties to
@@ -138,7 +144,8 @@ __device__ __forceinline__ float2 i8_to_f2_scaled(uint32_t w) {
 constexpr float kI8Scale = 256.0f;
 constexpr float kI8OffsetOverScale = 32896.0f;  // (2^23 + 2^15) / 256
 
-// pass-1 bin 0 of T scaled samples (T c + 256 sum x, exact) -> sum x, exactly
+// pass-1 bin 0 of T scaled samples (T c + 256 sum x, exact below 2^31: every partial
+// sum is a multiple of 256) -> sum x, exactly
 template <int T>
 __device__ __forceinline__ float2 kOffsetFix(float2 v) {
     constexpr float k = -(float)T * kI8OffsetOverScale;
@@ -159,7 +166,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 enum Feat { kPlain = 0, kDelay = 1 };
 
 template <int N, bool I8, int MODE, int FEAT>
-__global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const void *__restrict__ volt,
+__global__ void __launch_bounds__(kThreads, (N >= 2048 || (MODE == kPower && N >= 512)) ? 1 : (N >= 512 ? 2 : 3)) k_fengine(const void *__restrict__ volt,
                                                       const float *__restrict__ scale,
                                                       void *__restrict__ out,
                                                       double *__restrict__ power, int n_in, int K,
@@ -167,7 +174,8 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
                                                       const int *__restrict__ dint,
                                                       const float2 *__restrict__ dph, int async_raw) {
     using C = FCfg<N, I8, MODE>;
-    constexpr int T = C::T, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
+    constexpr int T1 = C::T1, T2 = C::T2, TG = C::TG, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
+    constexpr int TV = T1 > T2 ? T1 : T2;  // register values per thread
     constexpr bool DLY = FEAT == kDelay;  // delay code compiled in
     // int8 samples enter the plain FFT scaled by 256 on an offset (i8_to_f2_scaled); the
     // delay instantiation converts them exactly (measured faster there)
@@ -176,40 +184,46 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
     // advance in its FIR pass and only the phase here
     const bool has_shift = DLY && dint != nullptr, has_dly = DLY && dph != nullptr;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *ex = reinterpret_cast<float *>(smem_raw);                                 // [G][T][EXS]
+    float *ex = reinterpret_cast<float *>(smem_raw);                                 // [G][T1][EXS]
     float *scs = reinterpret_cast<float *>(smem_raw + C::ex_bytes);                  // [N] (power)
     float2 *tws = reinterpret_cast<float2 *>(smem_raw + C::ex_bytes + C::pw_bytes);  // [k1][t] twiddles
     float2 *dsm = reinterpret_cast<float2 *>(smem_raw + C::ex_bytes + C::pw_bytes + C::tw_bytes);  // [k2] phases
     uint32_t *stg = reinterpret_cast<uint32_t *>(smem_raw + C::ex_bytes + C::pw_bytes + C::tw_bytes +
                                                  C::dl_bytes);  // staging
     // 16-bit slot of code (k, s) in the swizzled staging rows
-    auto slot = [](int k, int s) { return k * (2 * ROWW) + 2 * ((s >> 1) ^ ((k >> 1) & 15)) + (s & 1); };
+    auto slot = [](int k, int s) {
+        return k * (2 * ROWW) + 2 * ((s >> 1) ^ ((k >> C::SW) & (ROWW - 1))) + (s & 1);
+    };
+    // the threads of one FFT group meet: a warp (or part of one), or the whole CTA
+    auto group_sync = [] {
+        if constexpr (TG <= 32) __syncwarp(); else __syncthreads();
+    };
 
     const int i = i0 + blockIdx.y;
     const int a0 = blockIdx.x * SB;
     // Raw int8 frames without delays are copied asynchronously into the FFT's exchange
     // buffer (free between exchanges): the copy for the next frame is issued after the
     // current frame's exchange and lands while its pass 2 and re-packing run. Each of
-    // the T threads moves T / 8 16-byte pieces of the 2 N-byte frame.
-    constexpr bool kAsync = I8 && !DLY && T >= 8;
+    // the TG threads moves N / (8 TG) 16-byte pieces of the 2 N-byte frame.
+    constexpr bool kAsync = I8 && !DLY && N / (8 * TG) >= 1;
     static_assert(!kAsync || sizeof(float) * C::GS >= 2 * N, "exchange buffer holds one raw frame");
     const bool use_async = kAsync && async_raw;
     // copy of frame s_ of this CTA into the exchange buffer of FFT slot s_ % G
     auto issue_raw = [&](int s_) {
-        const int a_ = a0 + s_, t_ = threadIdx.x % T;
+        const int a_ = a0 + s_, t_ = threadIdx.x % TG;
         if (s_ < SB && a_ < K) {
             const char *src = reinterpret_cast<const char *>(volt) + ((size_t)i * K + a_) * (size_t)N * 2;
             char *dst = reinterpret_cast<char *>(ex + (size_t)(s_ % G) * C::GS);
 #pragma unroll
-            for (int c = 0; c < T / 8; ++c) cp_async16(dst + (c * T + t_) * 16, src + (c * T + t_) * 16);
+            for (int c = 0; c < N / (8 * TG); ++c) cp_async16(dst + (c * TG + t_) * 16, src + (c * TG + t_) * 16);
         }
         cp_async_commit();
     };
-    if (use_async) issue_raw(threadIdx.x / T);
+    if (use_async) issue_raw(threadIdx.x / TG);
     // Delay compensation: the frames are read D samples later in input i's stream
-    // (samples outside the record are zero) and channel k = t + T k2 is multiplied by
-    // c[t] d[k2] = exp(+j 2 pi k f / N): c is folded into the inter-pass twiddles
-    // (it is common to thread t's pass-2 DFT), d applied to the outputs.
+    // (samples outside the record are zero) and channel k = k1 + T1 k2 is multiplied by
+    // c[k1] d[k2] = exp(+j 2 pi k f / N): c is folded into the inter-pass twiddles
+    // (it is common to thread k1's pass-2 DFT), d applied to the outputs.
     const long long n_rec = (long long)K * N;  // samples per input
     const int D = has_shift ? __ldg(dint + i) : 0;
     {
@@ -230,8 +244,8 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
     for (int m = threadIdx.x; m < N; m += kThreads) {
         float2 w = __ldg(tw_glob + m);
         if (DLY && has_dly) {
-            w = cmul(w, __ldg(dph + (size_t)i * 2 * T + m / T));  // table [k1][t]: c[k1]
-            if (m < T) dsm[m] = __ldg(dph + (size_t)i * 2 * T + T + m);
+            w = cmul(w, __ldg(dph + (size_t)i * (T1 + T2) + m / T2));  // table [k1][t]: c[k1]
+            if (m < T2) dsm[m] = __ldg(dph + (size_t)i * (T1 + T2) + T1 + m);
         }
         if constexpr (SCALED) w = make_float2(w.x * (1.0f / kI8Scale), w.y * (1.0f / kI8Scale));
         tws[m] = w;
@@ -239,22 +253,25 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
     }
     __syncthreads();
 
-    const int g = threadIdx.x / T;
-    const int t = threadIdx.x % T;
+    const int g = threadIdx.x / TG;
+    const int t = threadIdx.x % TG;
+    // pass 1 uses threads t < T2 (the columns), pass 2 threads k1 = t < T1 (the rows)
+    const bool act1 = T2 == TG || t < T2, act2 = T1 == TG || t < T1;
     float *exg = ex + (size_t)g * C::GS;
-    const float4 *exrow = reinterpret_cast<const float4 *>(exg + t * EXS);
-    float pw[T];
+    const float4 *exrow = reinterpret_cast<const float4 *>(exg + (act2 ? t : 0) * EXS);
+    float pw[T2];
     if constexpr (MODE == kPower) {
 #pragma unroll
-        for (int q = 0; q < T; ++q) pw[q] = 0.0f;
+        for (int q = 0; q < T2; ++q) pw[q] = 0.0f;
     }
 
     for (int s0 = 0; s0 < SB; s0 += G) {
         const int s = s0 + g;
         const int a = a0 + s;
         const bool valid = (s < SB) && (a < K);
-        float2 v[T];
-        // ---- pass 1: thread t takes x[t + T m]
+        const bool valid1 = valid && act1;
+        float2 v[TV];
+        // ---- pass 1: thread t takes x[t + T2 m]
         // sample offset of this frame in input i's stream (shifted by D with delays)
         const long long off = (long long)(valid ? a : 0) * N + D;
         const long long base = (long long)i * n_rec + off + t;
@@ -264,22 +281,22 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
             const unsigned short *src = reinterpret_cast<const unsigned short *>(volt) + base;
             if (use_async) {
                 cp_async_wait_all();
-                __syncwarp();  // every lane's pieces of the frame have landed
+                group_sync();  // every thread's pieces of the frame have landed
                 const unsigned short *raw = reinterpret_cast<const unsigned short *>(exg) + t;
 #pragma unroll
-                for (int m = 0; m < T; ++m) v[m] = i8_to_f2_scaled(valid ? (uint32_t)raw[T * m] : 0u);
-                __syncwarp();  // read before the exchange overwrites the buffer
+                for (int m = 0; m < T1; ++m) v[m] = i8_to_f2_scaled(valid1 ? (uint32_t)raw[T2 * m] : 0u);
+                group_sync();  // read before the exchange overwrites the buffer
             } else if (inside) {
 #pragma unroll
-                for (int m = 0; m < T; ++m) {
-                    const uint32_t w = valid ? (uint32_t)__ldg(src + (size_t)T * m) : 0u;
+                for (int m = 0; m < T1; ++m) {
+                    const uint32_t w = valid1 ? (uint32_t)__ldg(src + (size_t)T2 * m) : 0u;
                     v[m] = SCALED ? i8_to_f2_scaled(w) : i8_to_f2(w);
                 }
             } else {
 #pragma unroll
-                for (int m = 0; m < T; ++m) {
-                    const long long n = off + t + T * m;
-                    const uint32_t w = (valid && n >= 0 && n < n_rec) ? (uint32_t)__ldg(src + (long long)T * m) : 0u;
+                for (int m = 0; m < T1; ++m) {
+                    const long long n = off + t + T2 * m;
+                    const uint32_t w = (valid1 && n >= 0 && n < n_rec) ? (uint32_t)__ldg(src + (long long)T2 * m) : 0u;
                     v[m] = SCALED ? i8_to_f2_scaled(w) : i8_to_f2(w);
                 }
             }
@@ -287,55 +304,62 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
             const float2 *src = reinterpret_cast<const float2 *>(volt) + base;
             if (inside) {
 #pragma unroll
-                for (int m = 0; m < T; ++m) v[m] = valid ? __ldg(src + (size_t)T * m) : make_float2(0.f, 0.f);
+                for (int m = 0; m < T1; ++m) v[m] = valid1 ? __ldg(src + (size_t)T2 * m) : make_float2(0.f, 0.f);
             } else {
 #pragma unroll
-                for (int m = 0; m < T; ++m) {
-                    const long long n = off + t + T * m;
-                    v[m] = (valid && n >= 0 && n < n_rec) ? __ldg(src + (long long)T * m) : make_float2(0.f, 0.f);
+                for (int m = 0; m < T1; ++m) {
+                    const long long n = off + t + T2 * m;
+                    v[m] = (valid1 && n >= 0 && n < n_rec) ? __ldg(src + (long long)T2 * m) : make_float2(0.f, 0.f);
                 }
             }
         }
-        fft_dif<T>(v);  // v[bitrev(k1)] = Y[t][k1] (x 256, bin 0 offset, for int8 input)
-        if constexpr (SCALED) v[0] = kOffsetFix<T>(v[0]);
-        sfor<0, T>([&](auto K1) {
+        fft_dif<T1>(v);  // v[bitrev(k1)] = Y[t][k1] (x 256, bin 0 offset, for int8 input)
+        if constexpr (SCALED) v[0] = kOffsetFix<T1>(v[0]);
+        sfor<0, T1>([&](auto K1) {
             constexpr int k1 = decltype(K1)::value;
             // twiddle W_N^(t k1), table laid out [k1][t]
-            if constexpr (k1 != 0) v[bitrev(k1, ilog2(T))] = cmul(v[bitrev(k1, ilog2(T))], tws[k1 * T + t]);
+            if constexpr (k1 != 0)
+                if (act1) v[bitrev(k1, ilog2(T1))] = cmul(v[bitrev(k1, ilog2(T1))], tws[k1 * T2 + t]);
         });
         // ---- exchange (Re, then Im; the other half stays in place) and pass 2:
-        // thread t now plays k1 = t and takes Y[tt][k1]
-        sfor<0, T>([&](auto K1) {
-            constexpr int k1 = decltype(K1)::value;
-            exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T))].x;
-        });
-        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+        // thread t now plays k1 = t and takes Y[tt][k1], tt < T2
+        if (act1)
+            sfor<0, T1>([&](auto K1) {
+                constexpr int k1 = decltype(K1)::value;
+                exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T1))].x;
+            });
+        group_sync();
+        if (act2) {
 #pragma unroll
-        for (int j = 0; j < T / 4; ++j) {
-            const float4 r = exrow[j];
-            v[4 * j].x = r.x, v[4 * j + 1].x = r.y, v[4 * j + 2].x = r.z, v[4 * j + 3].x = r.w;
+            for (int j = 0; j < T2 / 4; ++j) {
+                const float4 r = exrow[j];
+                v[4 * j].x = r.x, v[4 * j + 1].x = r.y, v[4 * j + 2].x = r.z, v[4 * j + 3].x = r.w;
+            }
         }
-        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
-        sfor<0, T>([&](auto K1) {
-            constexpr int k1 = decltype(K1)::value;
-            exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T))].y;
-        });
-        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+        group_sync();
+        if (act1)
+            sfor<0, T1>([&](auto K1) {
+                constexpr int k1 = decltype(K1)::value;
+                exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T1))].y;
+            });
+        group_sync();
+        if (act2) {
 #pragma unroll
-        for (int j = 0; j < T / 4; ++j) {
-            const float4 r = exrow[j];
-            v[4 * j].y = r.x, v[4 * j + 1].y = r.y, v[4 * j + 2].y = r.z, v[4 * j + 3].y = r.w;
+            for (int j = 0; j < T2 / 4; ++j) {
+                const float4 r = exrow[j];
+                v[4 * j].y = r.x, v[4 * j + 1].y = r.y, v[4 * j + 2].y = r.z, v[4 * j + 3].y = r.w;
+            }
         }
-        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
+        group_sync();
         if (use_async && s0 + G < SB) issue_raw(s0 + G + g);  // next frame into the free buffer
-        fft_dif<T>(v);  // v[bitrev(k2)] = X[t + T k2]
-        if (valid) {
-            sfor<0, T>([&](auto K2) {
+        fft_dif<T2>(v);  // v[bitrev(k2)] = X[t + T1 k2]
+        if (valid && act2) {
+            sfor<0, T2>([&](auto K2) {
                 constexpr int k2 = decltype(K2)::value;
-                const int k = t + T * k2;
-                float2 x = v[bitrev(k2, ilog2(T))];
+                const int k = t + T1 * k2;
+                float2 x = v[bitrev(k2, ilog2(T2))];
                 if constexpr (DLY && k2 != 0) {
-                    if (has_dly) x = cmul(x, dsm[k2]);  // delay phase exp(+j 2 pi T k2 f / N)
+                    if (has_dly) x = cmul(x, dsm[k2]);  // delay phase exp(+j 2 pi T1 k2 f / N)
                 }
                 if constexpr (MODE == kRequant || MODE == kRequantPlanar) {
                     const uint32_t q = pack_q<MODE == kRequantPlanar>(x, __ldg(scale + k));
@@ -366,9 +390,9 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
                 const int q = threadIdx.x % CPR;
                 int k = threadIdx.x / CPR;
                 // physical words of logical words 4q .. 4q + 3 in row k; the swizzle
-                // (k >> 1) & 15 is the same for k + RPI (RPI / 2 is a multiple of 16)
-                static_assert((RPI / 2) % 16 == 0 || RPI >= N, "");
-                const int h = (k >> 1) & 15;
+                // (k >> SW) & (ROWW - 1) is the same for k + RPI
+                static_assert((RPI >> C::SW) % ROWW == 0 || RPI >= N, "");
+                const int h = (k >> C::SW) & (ROWW - 1);
                 const int o0 = (4 * q) ^ h, o1 = (4 * q + 1) ^ h, o2 = (4 * q + 2) ^ h, o3 = (4 * q + 3) ^ h;
                 const uint32_t *src = stg + (size_t)k * ROWW;
                 uint4 *d = reinterpret_cast<uint4 *>(dst + ((size_t)(PL * k) * n_in + i) * K + a0 + 8 * q);
@@ -415,10 +439,11 @@ __global__ void __launch_bounds__(kThreads, N >= 1024 ? 2 : 3) k_fengine(const v
     }
 
     if constexpr (MODE == kPower) {
-        sfor<0, T>([&](auto K2) {
-            constexpr int k2 = decltype(K2)::value;
-            atomicAdd(&scs[t + T * k2], pw[k2]);
-        });
+        if (act2)
+            sfor<0, T2>([&](auto K2) {
+                constexpr int k2 = decltype(K2)::value;
+                atomicAdd(&scs[t + T1 * k2], pw[k2]);
+            });
         __syncthreads();
         for (int m = threadIdx.x; m < N; m += kThreads) atomicAdd(&power[m], (double)scs[m]);
     }
@@ -453,8 +478,12 @@ corr_status launch_mode(const FShape &f, const void *volt, const float *scale, v
     switch (f.n_chan) {
         CORR_F_CASE(16)
         CORR_F_CASE(64)
+        CORR_F_CASE(128)
         CORR_F_CASE(256)
+        CORR_F_CASE(512)
         CORR_F_CASE(1024)
+        CORR_F_CASE(2048)
+        CORR_F_CASE(4096)
         default: return CORR_EUNSUPPORTED;
     }
 #undef CORR_F_CASE

@@ -134,10 +134,11 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// In-register P-point DFT (Eq. 1 on P points), radix-2 decimation in frequency.
-// On return v[bitrev(k)] holds X[k].
-template <int P>
-__device__ __forceinline__ void fft_dif(float2 (&v)[P]) {
+// In-register P-point DFT (Eq. 1 on P points) of v[0 .. P-1], radix-2 decimation in
+// frequency (v may hold more than P values). On return v[bitrev(k)] holds X[k].
+template <int P, int L>
+__device__ __forceinline__ void fft_dif(float2 (&v)[L]) {
+    static_assert(P <= L, "DFT longer than the register array");
     constexpr int LG = ilog2(P);
     sfor<0, LG>([&](auto S) {
         constexpr int half = P >> (decltype(S)::value + 1);

@@ -37,9 +37,9 @@ struct Handle {
     bool acc_zero = true;        // accumulator known to be all-zero (X-engine may store instead of add)
     int64_t acc_spectra = 0;     // spectra accumulated since the last dump (INT8 overflow guard)
     double2 *vis64 = nullptr;    // FP64 long-integration buffer [n_chan][B]
-    float2 *twiddle = nullptr;   // F-engine twiddles W_N^(t k1), [k1][t], N = T x T
+    float2 *twiddle = nullptr;   // F-engine twiddles W_N^(t k1), [k1][t], N = T1 x T2
     int32_t *dly_int = nullptr;  // delay compensation (null: off): integer advance per input
-    float2 *dly_ph = nullptr;    //   and phase tables [n_in][2 T]: exp(+j 2 pi k1 f / N), exp(+j 2 pi T k2 f / N)
+    float2 *dly_ph = nullptr;    //   and phase tables [n_in][T1 + T2]: exp(+j 2 pi k1 f / N), exp(+j 2 pi T1 k2 f / N)
     float *pfb_win = nullptr;    // polyphase filter-bank window [pfb_taps][n_chan] (null: off)
     int32_t pfb_taps = 0;
     void *pfb_y = nullptr;       //   its FIR output, complex FP32 [n_in][n_spectra][n_chan]
@@ -183,6 +183,13 @@ corr_status tma_encode_planar(void *tmap128, const void *planes, int n_in, int n
 // One persistent launch over a precomputed work list (see batch.cu).
 corr_status launch_xengine_tma_batch(const void *d_tmaps, const BatchSub *d_subs, const int4 *d_items,
                                      const int *d_cta_off, int grid, int *status, cudaStream_t st);
+
+// F-engine split N = T1 x T2 (T1-point DFTs in pass 1 by T2 threads, T2-point DFTs in
+// pass 2 by T1 threads); returns T2, or 0 for a length the F-engine does not support.
+__host__ __device__ constexpr int fengine_t2(int n) {
+    return n == 16 ? 4 : n == 64 ? 8 : n == 128 ? 16 : n == 256 ? 16 : n == 512 ? 32 : n == 1024 ? 32
+         : n == 2048 ? 64 : n == 4096 ? 64 : 0;
+}
 
 // Bounded-wait iteration limit for device-side spins (mbarrier waits).
 constexpr long long kSpinLimit = 1LL << 26;

@@ -24,7 +24,8 @@ def _delays(n_in, N, seed):
     return d
 
 
-@pytest.mark.parametrize("N,n_in,K", [(16, 5, 21), (64, 3, 9), (256, 3, 13), (1024, 4, 11)])
+@pytest.mark.parametrize("N,n_in,K", [(16, 5, 21), (64, 3, 9), (128, 3, 8), (256, 3, 13), (512, 2, 9),
+                                     (1024, 4, 11), (2048, 2, 5), (4096, 2, 4)])
 def test_fengine_fp32_delays_match_oracle(cuda_ok, N, n_in, K):
     v = synth.volt_fp32(n_in, N, K, seed=N + 1)
     d = _delays(n_in, N, seed=N)
@@ -42,7 +43,8 @@ def test_fengine_fp32_delays_match_oracle(cuda_ok, N, n_in, K):
 
 
 @pytest.mark.parametrize("planar", [False, True])
-@pytest.mark.parametrize("N,n_ant,n_pol,K", [(64, 3, 1, 24), (256, 2, 2, 16), (1024, 1, 2, 40)])
+@pytest.mark.parametrize("N,n_ant,n_pol,K", [(64, 3, 1, 24), (256, 2, 2, 16), (512, 1, 2, 16), (1024, 1, 2, 40),
+                                            (4096, 1, 2, 8)])
 def test_fengine_int8_delays_requant(cuda_ok, planar, N, n_ant, n_pol, K):
     v = synth.volt_int8(n_ant, n_pol, N, K, seed=9)
     n_in = n_ant * n_pol

@@ -31,7 +31,8 @@ def c64(V2):
 
 
 # --------------------------------------------------------------------------- F-engine
-@pytest.mark.parametrize("N,n_in,K", [(16, 3, 21), (64, 2, 9), (256, 3, 13), (1024, 2, 11)])
+@pytest.mark.parametrize("N,n_in,K", [(16, 3, 21), (64, 2, 9), (128, 3, 10), (256, 3, 13), (512, 2, 7),
+                                     (1024, 2, 11), (2048, 2, 5), (4096, 2, 3)])
 def test_fengine_fp32_matches_dft(cuda_ok, N, n_in, K):
     v = synth.volt_fp32(n_in, N, K, seed=N)
     c = api.Correlator(n_in, 1, N, K, precision="fp32")
@@ -42,7 +43,8 @@ def test_fengine_fp32_matches_dft(cuda_ok, N, n_in, K):
     c.close()
 
 
-@pytest.mark.parametrize("N,n_ant,n_pol,K", [(16, 2, 2, 37), (64, 3, 1, 20), (256, 2, 2, 17), (1024, 1, 2, 35)])
+@pytest.mark.parametrize("N,n_ant,n_pol,K", [(16, 2, 2, 37), (64, 3, 1, 20), (128, 2, 2, 19), (256, 2, 2, 17),
+                                            (512, 1, 2, 21), (1024, 1, 2, 35), (2048, 1, 2, 13), (4096, 1, 2, 9)])
 def test_fengine_int8_requant_corner_turn(cuda_ok, N, n_ant, n_pol, K):
     v = synth.volt_int8(n_ant, n_pol, N, K, seed=7)
     rng = np.random.default_rng(N)

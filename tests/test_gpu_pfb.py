@@ -19,7 +19,8 @@ def _sinc_hann(P, N):
 
 @pytest.mark.parametrize("N,n_in,K,P,with_delays", [(16, 3, 21, 4, False), (64, 2, 9, 3, True),
                                                      (256, 3, 13, 4, False), (1024, 2, 11, 4, True),
-                                                     (1024, 1, 6, 1, False)])
+                                                     (1024, 1, 6, 1, False), (512, 2, 7, 4, True),
+                                                     (2048, 1, 5, 3, True)])
 def test_pfb_fp32_matches_oracle(cuda_ok, N, n_in, K, P, with_delays):
     v = synth.volt_fp32(n_in, N, K, seed=N + P)
     h = _sinc_hann(P, N)

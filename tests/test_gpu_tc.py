@@ -144,10 +144,11 @@ def test_tma_planar_extreme_values_and_accumulate(cuda_ok):
     c.close()
 
 
-def test_fengine_planar_matches_int8_layout_and_oracle(cuda_ok):
-    n_ant, n_pol, N, K = 3, 2, 1024, 40
+@pytest.mark.parametrize("N", [128, 512, 1024, 2048, 4096])
+def test_fengine_planar_matches_int8_layout_and_oracle(cuda_ok, N):
+    n_ant, n_pol, K = 3, 2, 40
     v = synth.volt_int8(n_ant, n_pol, N, K, seed=9)
-    scale = np.full(N, 1.0 / 32.0, np.float32)
+    scale = np.full(N, 0.5 / np.sqrt(N), np.float32)  # rms 16 sqrt(N) -> 8
     vt, st = torch.from_numpy(v).to(DEV), torch.from_numpy(scale).to(DEV)
     a = api.Correlator(n_ant, n_pol, N, K, precision="int8")
     b = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
