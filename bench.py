@@ -308,6 +308,9 @@ def run_ours(args):
     t0.record(stream)
     for s in range(args.steps):
         step(evs[s])
+    # a dump deferred into the next X-engine launch is still pending after the last step:
+    # complete it inside the timed region, so that every timed integration is dumped
+    corr.flush()
     t1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
@@ -453,8 +456,9 @@ def run_ours(args):
               "algorithmic": f"{f_bytes:.4g} bytes per launch (read 2 B + write 2 B per complex sample); the "
                              f"{args.layout} exchange layout moves {f_layout_bytes:.4g}"}
     d_bytes = float(N * B * (8 + 32))  # read INT32 pairs, read and write FP64 pairs
+    deferred = d_ms < 0.05  # the dump ran inside the next X-engine launch (no kernel of its own)
     roof_d = None
-    if d_ms:
+    if not deferred:
         d_ach = d_bytes / (d_ms * 1e-3) / 1e9
         roof_d = {"bound": "hbm", "achieved": d_ach, "peak": peaks["hbm"], "unit": "GB/s", "frac": d_ach / peaks["hbm"],
                   "traffic": _traffic("k_dump") if full_size else None,
@@ -488,7 +492,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8", "data": "synthetic",
         "config": {"workload": _workload_name(args.workload), "l2": "inputs larger than L2 (4.29 GB per step)",
-                   "layout": args.layout, "dump": "fused into the X-engine epilogue" if fused else "separate kernel",
+                   "layout": args.layout,
+                   "dump": "fused into the X-engine epilogue" if fused else (
+                       "deferred: each integration's FP64 dump runs in idle warps of the next X-engine launch (the last "
+                       "one by a flush inside the timed region)" if deferred else "separate kernel"),
                    "delay_compensation": bool(args.delays),
                    "pfb_taps": args.pfb,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -497,7 +504,7 @@ def run_ours(args):
         "fengine_gbs": f_ach,
         "fengine_hbm_frac": f_ach / peaks["hbm"],
         "fengine_fp32": fengine_fp32_rate(N, n_in * K, f_ms, clocks),
-        "dump_gbs": d_bytes / (d_ms * 1e-3) / 1e9 if d_ms else None,
+        "dump_gbs": d_bytes / (d_ms * 1e-3) / 1e9 if not deferred else None,
         "cudacore_comparator": None if cc_ms is None else {
             "xengine_ms": cc_ms, "cmac_per_s": cmac_step / (cc_ms * 1e-3), "speedup_tensor_vs_cudacore": cc_ms / x_ms,
             "accuracy": "both exact (bit-identical INT32)"},

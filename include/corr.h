@@ -244,8 +244,20 @@ CORR_API corr_status corr_get_accum(corr_t *h, void *out, void *stream);
  * not NULL, the FP64 long-integration buffer is copied to it
  * ([n_chan][B] complex double, device). Asynchronous. The paper writes each
  * accumulation's visibilities out (Section 5, Section 6.3); the FP64 long
- * integration is this library's own addition, with no passage behind it. */
+ * integration is this library's own addition, with no passage behind it.
+ * On the INT8 and FP16_HILO tensor-core X-engine (without CORR_FLAG_FUSED_DUMP) a
+ * dump with vis_out NULL is deferred: the finished accumulator is kept aside (the handle
+ * then holds a second accumulator buffer, allocated on first use) and the next
+ * corr_xengine launch adds it to the FP64 buffer from warps that would otherwise
+ * idle, overlapping the X-engine. corr_flush, corr_dump with vis_out and
+ * corr_fx_host complete a deferred dump first, so every reader of the FP64
+ * buffer sees the same sums as with an immediate dump (bit for bit). */
 CORR_API corr_status corr_dump(corr_t *h, double *vis_out, void *stream);
+
+/* Complete any deferred dump (see corr_dump) on `stream` now: afterwards the FP64
+ * long-integration buffer holds every dumped integration. No-op when none is
+ * pending. (No counterpart in the paper.) */
+CORR_API corr_status corr_flush(corr_t *h, void *stream);
 
 /* Checkpoint / resume of the long integration: set the handle's FP64 buffer to
  *   vis_in [n_chan][B] complex double (device, 16-byte aligned; e.g. a buffer that

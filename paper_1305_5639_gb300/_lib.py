@@ -56,6 +56,7 @@ SIGNATURES = [
     ("corr_xengine_cross", _S, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     ("corr_get_accum", _S, [_P, _P, _P]),
     ("corr_dump", _S, [_P, _P, _P]),
+    ("corr_flush", _S, [_P, _P]),
     ("corr_restore_vis", _S, [_P, _P, _P]),
     ("corr_selftest_bounded_wait", _S, [ctypes.c_int32, ctypes.c_int64]),
     ("corr_check_status", _S, [_P, _P]),

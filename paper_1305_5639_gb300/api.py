@@ -99,6 +99,10 @@ def corr_dump(h, vis_out=None, stream=None) -> None:
     check(_lib.load().corr_dump(h, _ptr(vis_out), _stream(stream)), "corr_dump")
 
 
+def corr_flush(h, stream=None) -> None:
+    check(_lib.load().corr_flush(h, _stream(stream)), "corr_flush")
+
+
 def corr_restore_vis(h, vis_in=None, stream=None) -> None:
     check(_lib.load().corr_restore_vis(h, _ptr(vis_in), _stream(stream)), "corr_restore_vis")
 
@@ -227,6 +231,10 @@ class Correlator:
             out = torch.empty((self.n_chan, self.n_base), dtype=torch.complex128, device=self.device)
         corr_dump(self.h, out if copy else None, stream)
         return out
+
+    def flush(self, stream=None):
+        """Complete a deferred dump now (see corr_dump)."""
+        corr_flush(self.h, stream)
 
     def set_delays(self, delays=None):
         """Per-input delays in samples (sequence of n_in floats) for delay compensation

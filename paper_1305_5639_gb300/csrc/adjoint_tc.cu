@@ -31,8 +31,6 @@
 namespace corr {
 namespace {
 
-constexpr int kTile = 32;  // prep tiles: 32 x 32 entries, 256 threads
-
 __device__ __forceinline__ void split_hl(float x, __half &h, __half &l) {
     h = __float2half_rn(x);
     l = __float2half_rn(x - __half2float(h));
@@ -78,95 +76,131 @@ __global__ void __launch_bounds__(256) k_adj_expo(const float2 *__restrict__ Gp,
     }
 }
 
-// A_f = 2^e_f G^_f diag(g) as four FP16 planes [f - c0][plane][m][j]; one CTA per
-// 32 x 32 tile (rows m, columns j); the packed storage holds only j <= m, so tiles
-// above the diagonal read the mirrored tile and conjugate it.
+// The operand passes move 64 x 64 tiles through shared memory (rows padded to 65
+// complex values) and write each output row as 16-byte pieces of 8 consecutive
+// columns per plane, 8 threads per row.
+constexpr int kPT = 64;   // prep tile edge
+constexpr int kPTS = 65;  // padded row stride of the shared tile (complex values)
+
+// 8 complex values -> the 4 FP16 planes (Re_h, Im_h, Re_l, Im_l), 16 bytes each.
+__device__ __forceinline__ void store8_planes(const float (&re)[8], const float (&im)[8], __half *dst,
+                                              size_t plane) {
+    uint32_t w[4][4];
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+        __half rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
+        split_hl(re[q], rh0, rl0);
+        split_hl(im[q], ih0, il0);
+        split_hl(re[q + 1], rh1, rl1);
+        split_hl(im[q + 1], ih1, il1);
+        w[0][q / 2] = (uint32_t)__half_as_ushort(rh0) | ((uint32_t)__half_as_ushort(rh1) << 16);
+        w[1][q / 2] = (uint32_t)__half_as_ushort(ih0) | ((uint32_t)__half_as_ushort(ih1) << 16);
+        w[2][q / 2] = (uint32_t)__half_as_ushort(rl0) | ((uint32_t)__half_as_ushort(rl1) << 16);
+        w[3][q / 2] = (uint32_t)__half_as_ushort(il0) | ((uint32_t)__half_as_ushort(il1) << 16);
+    }
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl)
+        *reinterpret_cast<uint4 *>(dst + pl * plane) = make_uint4(w[pl][0], w[pl][1], w[pl][2], w[pl][3]);
+}
+
+// A_f = 2^e_f G^_f diag(g) as four FP16 planes [f - c0][plane][m][j]. One CTA per
+// lower-triangle tile (mb >= jb) of 64 x 64 entries: the packed gradient's tile
+// T[r][c] = G(m0 + r, j0 + c) is read once and gives both A tiles it defines:
+//   tile (mb, jb):  A[m][j] = G^_mj g_j with G^_mj = T[r][c] (on the diagonal tile:
+//                   conj T[c][r] above the diagonal, 2 Re T[r][r] on it)
+//   tile (jb, mb):  A[j][m] = conj(T[r][c]) g_m      (mb > jb only)
+// n_in must be a multiple of 8 (whole 16-byte pieces).
 __global__ void __launch_bounds__(256) k_adj_aprep(const float2 *__restrict__ Gp, const float2 *__restrict__ gains,
                                                    const int *__restrict__ expo, __half *__restrict__ A, int n_in,
                                                    long long B, int c0) {
-    __shared__ float2 T[kTile][kTile + 1];
-    const int mb = blockIdx.y, jb = blockIdx.x, fl = blockIdx.z;
+    __shared__ float2 T[kPT * kPTS];
+    const int t = blockIdx.x, fl = blockIdx.y;
+    int mb = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((mb + 1) * (mb + 2) / 2 <= t) ++mb;
+    while (mb * (mb + 1) / 2 > t) --mb;
+    const int jb = t - mb * (mb + 1) / 2;
     const float2 *G = Gp + (size_t)(c0 + fl) * B;
-    const int m0 = mb * kTile, j0 = jb * kTile;
-    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-        const int r = e / kTile, c = e % kTile;
+    const int m0 = mb * kPT, j0 = jb * kPT;
+    const bool diag = mb == jb;
+    for (int e = threadIdx.x; e < kPT * kPT; e += blockDim.x) {
+        const int r = e / kPT, c = e % kPT;
+        const int m = m0 + r, j = j0 + c;
         float2 v = make_float2(0.f, 0.f);
-        if (mb > jb) {  // T[r][c] = G(m0 + r, j0 + c)
-            const int m = m0 + r, j = j0 + c;
-            if (m < n_in && j < n_in) v = __ldg(G + (size_t)m * (m + 1) / 2 + j);
-        } else if (mb < jb) {  // T[r][c] = G(j0 + r, m0 + c), the mirrored tile
-            const int j = j0 + r, m = m0 + c;
-            if (j < n_in && m < n_in) v = __ldg(G + (size_t)j * (j + 1) / 2 + m);
-        } else {  // diagonal tile: its lower triangle
-            const int m = m0 + r, j = m0 + c;
-            if (c <= r && m < n_in) v = __ldg(G + (size_t)m * (m + 1) / 2 + j);
-        }
-        T[r][c] = v;
+        if (m < n_in && j < n_in && (!diag || c <= r)) v = __ldg(G + (size_t)m * (m + 1) / 2 + j);
+        T[r * kPTS + c] = v;
     }
     __syncthreads();
     const float sc = ldexpf(1.0f, __ldg(expo + fl));
-    // each thread: 4 consecutive j of one row m
-    const int r = threadIdx.x / (kTile / 4), c4 = (threadIdx.x % (kTile / 4)) * 4;
-    const int m = m0 + r;
-    if (m >= n_in || j0 + c4 >= n_in) return;
-    __half hv[4][4];  // [plane][q]
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int c = c4 + q, j = j0 + c;
-        float2 gh;
-        if (mb > jb) gh = T[r][c];
-        else if (mb < jb) gh = make_float2(T[c][r].x, -T[c][r].y);
-        else if (r > c) gh = T[r][c];
-        else if (r < c) gh = make_float2(T[c][r].x, -T[c][r].y);
-        else gh = make_float2(2.0f * T[r][r].x, 0.0f);
-        const float2 g = gains ? __ldg(gains + j) : make_float2(1.f, 0.f);
-        const float zr = (gh.x * g.x - gh.y * g.y) * sc, zi = (gh.x * g.y + gh.y * g.x) * sc;
-        split_hl(zr, hv[0][q], hv[2][q]);
-        split_hl(zi, hv[1][q], hv[3][q]);
-    }
     const size_t plane = (size_t)n_in * n_in;
-    __half *dst = A + (size_t)fl * 4 * plane + (size_t)m * n_in + j0 + c4;
+    __half *Af = A + (size_t)fl * 4 * plane;
+    // 64 rows x 8 pieces of 8 columns per output tile, two (row, piece) items per thread
+    for (int it = threadIdx.x; it < kPT * 8; it += blockDim.x) {
+        const int r = it / 8, ch = it % 8;
+        // tile (mb, jb): row m = m0 + r, columns j = j0 + 8 ch + q
+        const int m = m0 + r, jc = j0 + 8 * ch;
+        if (m < n_in && jc < n_in) {
+            float re[8], im[8];
 #pragma unroll
-    for (int pl = 0; pl < 4; ++pl) {
-        uint2 w;
-        w.x = (uint32_t)__half_as_ushort(hv[pl][0]) | ((uint32_t)__half_as_ushort(hv[pl][1]) << 16);
-        w.y = (uint32_t)__half_as_ushort(hv[pl][2]) | ((uint32_t)__half_as_ushort(hv[pl][3]) << 16);
-        *reinterpret_cast<uint2 *>(dst + pl * plane) = w;
+            for (int q = 0; q < 8; ++q) {
+                const int c = 8 * ch + q;
+                float2 gh;
+                if (!diag || r > c) gh = T[r * kPTS + c];
+                else if (r < c) gh = make_float2(T[c * kPTS + r].x, -T[c * kPTS + r].y);
+                else gh = make_float2(2.0f * T[r * kPTS + r].x, 0.0f);
+                const float2 g = gains ? __ldg(gains + jc + q) : make_float2(1.f, 0.f);
+                re[q] = (gh.x * g.x - gh.y * g.y) * sc;
+                im[q] = (gh.x * g.y + gh.y * g.x) * sc;
+            }
+            store8_planes(re, im, Af + (size_t)m * n_in + jc, plane);
+        }
+        // tile (jb, mb): row j = j0 + r, columns m = m0 + 8 ch + q, A[j][m] = conj(G(m, j)) g_m
+        const int j = j0 + r, mc = m0 + 8 * ch;
+        if (!diag && j < n_in && mc < n_in) {
+            float re[8], im[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 v = T[(8 * ch + q) * kPTS + r];  // G(m, j), m = mc + q
+                const float2 g = gains ? __ldg(gains + mc + q) : make_float2(1.f, 0.f);
+                re[q] = (v.x * g.x + v.y * g.y) * sc;  // conj(v) g
+                im[q] = (v.x * g.y - v.y * g.x) * sc;
+            }
+            store8_planes(re, im, Af + (size_t)j * n_in + mc, plane);
+        }
     }
 }
 
-// conj(X_f)^T as four FP16 planes [f - c0][plane][a][j]: one CTA per 32 inputs j x
-// 32 spectra a, transposed through shared memory.
+// conj(X_f)^T as four FP16 planes [f - c0][plane][a][j]: one CTA per 64 inputs j x 64
+// spectra a, read as 16-byte pairs of spectra, transposed through shared memory.
+// n_in and K must be multiples of 8.
 __global__ void __launch_bounds__(256) k_adj_bprep(const float2 *__restrict__ X, __half *__restrict__ Bt, int n_in,
                                                    int K, int c0) {
-    __shared__ float2 T[kTile][kTile + 1];  // T[j][a]
+    __shared__ float2 T[kPT * kPTS];  // T[j][a]
     const int ab = blockIdx.x, jb = blockIdx.y, fl = blockIdx.z;
-    const int j0 = jb * kTile, a0 = ab * kTile;
+    const int j0 = jb * kPT, a0 = ab * kPT;
     const float2 *Xc = X + (size_t)(c0 + fl) * n_in * K;
-    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-        const int r = e / kTile, c = e % kTile;
+    for (int e = threadIdx.x; e < kPT * kPT / 2; e += blockDim.x) {
+        const int r = e / (kPT / 2), c = 2 * (e % (kPT / 2));
         const int j = j0 + r, a = a0 + c;
-        T[r][c] = (j < n_in && a < K) ? __ldg(Xc + (size_t)j * K + a) : make_float2(0.f, 0.f);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < n_in && a < K) v = __ldg(reinterpret_cast<const float4 *>(Xc + (size_t)j * K + a));
+        T[r * kPTS + c] = make_float2(v.x, v.y);
+        T[r * kPTS + c + 1] = make_float2(v.z, v.w);
     }
     __syncthreads();
-    const int r = threadIdx.x / (kTile / 4), c4 = (threadIdx.x % (kTile / 4)) * 4;  // row a, 4 j
-    const int a = a0 + r;
-    if (a >= K || j0 + c4 >= n_in) return;
-    __half hv[4][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float2 x = T[c4 + q][r];
-        split_hl(x.x, hv[0][q], hv[2][q]);
-        split_hl(-x.y, hv[1][q], hv[3][q]);
-    }
     const size_t plane = (size_t)K * n_in;
-    __half *dst = Bt + (size_t)fl * 4 * plane + (size_t)a * n_in + j0 + c4;
+    __half *Bf = Bt + (size_t)fl * 4 * plane;
+    for (int it = threadIdx.x; it < kPT * 8; it += blockDim.x) {
+        const int r = it / 8, ch = it % 8;  // output row a = a0 + r, columns j = j0 + 8 ch + q
+        const int a = a0 + r, jc = j0 + 8 * ch;
+        if (a >= K || jc >= n_in) continue;
+        float re[8], im[8];
 #pragma unroll
-    for (int pl = 0; pl < 4; ++pl) {
-        uint2 w;
-        w.x = (uint32_t)__half_as_ushort(hv[pl][0]) | ((uint32_t)__half_as_ushort(hv[pl][1]) << 16);
-        w.y = (uint32_t)__half_as_ushort(hv[pl][2]) | ((uint32_t)__half_as_ushort(hv[pl][3]) << 16);
-        *reinterpret_cast<uint2 *>(dst + pl * plane) = w;
+        for (int q = 0; q < 8; ++q) {
+            const float2 x = T[(8 * ch + q) * kPTS + r];
+            re[q] = x.x;
+            im[q] = -x.y;
+        }
+        store8_planes(re, im, Bf + (size_t)a * n_in + jc, plane);
     }
 }
 
@@ -225,7 +259,8 @@ corr_status launch_backward_tc(const Handle &h, const float2 *grad_vis, const fl
     char *base = static_cast<char *>(ws);
     float2 *part = grad_gains ? reinterpret_cast<float2 *>(base + w.part) : nullptr;
     int *expo = reinterpret_cast<int *>(base + w.expo);
-    const int nt_in = (h.n_in + kTile - 1) / kTile, nt_k = (h.n_spectra + kTile - 1) / kTile;
+    const int nt_in = (h.n_in + kPT - 1) / kPT, nt_k = (h.n_spectra + kPT - 1) / kPT;
+    const int n_tri = nt_in * (nt_in + 1) / 2;
     CORR_CUDA_TRY(cudaEventRecord(ev[0], st));
     CORR_CUDA_TRY(cudaStreamWaitEvent(side, ev[0], 0));
     corr_status s;
@@ -243,8 +278,7 @@ corr_status launch_backward_tc(const Handle &h, const float2 *grad_vis, const fl
         if (blk >= 2) CORR_CUDA_TRY(cudaStreamWaitEvent(side, ev[3 + k], 0));  // GEMM of block - 2 done
         {
             StageScope sc(h, CORR_STAGE_ADJ_PREP, side, 2);
-            k_adj_aprep<<<dim3(nt_in, nt_in, nc), 256, 0, side>>>(grad_vis, gains, expo + c0, A, h.n_in, h.n_base,
-                                                                 c0);
+            k_adj_aprep<<<dim3(n_tri, nc), 256, 0, side>>>(grad_vis, gains, expo + c0, A, h.n_in, h.n_base, c0);
             if ((s = check_launch("k_adj_aprep")) != CORR_OK) return s;
             k_adj_bprep<<<dim3(nt_k, nt_in, nc), 256, 0, side>>>(chan_in, Bt, h.n_in, h.n_spectra, c0);
             if ((s = check_launch("k_adj_bprep")) != CORR_OK) return s;

@@ -85,6 +85,20 @@ __global__ void __launch_bounds__(256) k_dump(const AccT *__restrict__ acc, doub
 
 corr_status launch_dump(const Handle &h, cudaStream_t st) { return launch_dump_range(h, 0, h.n_chan, st); }
 
+corr_status launch_dump_src(const Handle &h, const void *acc, cudaStream_t st) {
+    const long long n = (long long)h.n_chan * h.n_base;
+    if (n <= 0) return CORR_OK;
+    StageScope sc(h, CORR_STAGE_DUMP, st);
+    long long blocks = (n + 255) / 256;
+    const long long cap = (long long)h.n_sm * 16;
+    if (blocks > cap) blocks = cap;
+    if (h.precision == CORR_PREC_INT8)
+        k_dump<int2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const int2 *>(acc), h.vis64, n);
+    else
+        k_dump<float2><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const float2 *>(acc), h.vis64, n);
+    return check_launch("k_dump");
+}
+
 corr_status launch_dump_range(const Handle &h, int c0, int c1, cudaStream_t st) {
     const long long n = (long long)(c1 - c0) * h.n_base;
     if (n <= 0) return CORR_OK;

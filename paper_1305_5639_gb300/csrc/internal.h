@@ -35,6 +35,12 @@ struct Handle {
     // integration accumulator [n_chan][B]: int2 (INT8) or float2 (float paths)
     void *acc = nullptr;
     bool acc_zero = true;        // accumulator known to be all-zero (X-engine may store instead of add)
+    // deferred dump (tensor-core X-engine): corr_dump without a copy swaps acc with
+    // acc_alt and leaves the finished integration in pending_src; the next X-engine
+    // launch adds it to vis64 from idle warps (or a flush runs the dump kernel)
+    void *acc_alt = nullptr;
+    bool dump_pending = false;
+    const void *pending_src = nullptr;
     int64_t acc_spectra = 0;     // spectra accumulated since the last dump (INT8 overflow guard)
     double2 *vis64 = nullptr;    // FP64 long-integration buffer [n_chan][B]
     float2 *twiddle = nullptr;   // F-engine twiddles W_N^(t k1), [k1][t], N = T1 x T2
@@ -115,6 +121,8 @@ corr_status launch_xengine_cudacore(const Handle &h, const void *chan_in, const 
                                     bool store, cudaStream_t st);
 corr_status launch_dump(const Handle &h, cudaStream_t st);
 corr_status launch_dump_range(const Handle &h, int c0, int c1, cudaStream_t st);
+// The dump of an accumulator other than the handle's current one (a deferred dump).
+corr_status launch_dump_src(const Handle &h, const void *acc, cudaStream_t st);
 corr_status launch_fengine_range(const Handle &h, const void *volt, const float *scale, void *out, int i0, int n_run,
                                  cudaStream_t st);
 // TMA X-engine over channels [c0, c1) of planar FP16 operands [chan][npl][n_in][kstride]

@@ -14,9 +14,11 @@
 //
 // Layout [chan][plane][input][Kp] (planes Re_h, Im_h (, Re_l, Im_l)), Kp = the
 // spectra rounded up to a multiple of 8 so that every row starts on a 16-byte
-// boundary (a TMA requirement); the tail is written as zeros. One warp per row:
-// a pass for the maximum, then the conversion (the row is re-read from L1/L2), so
-// HBM sees 8 B read and 4 B (plain) or 8 B (hi/lo) written per complex sample.
+// boundary (a TMA requirement); the tail is written as zeros. Rows of up to 4096
+// spectra are held in the registers of one CTA (k_to_planar_row); longer rows take
+// one warp per row, a pass for the maximum and then the conversion (the row re-read
+// from L1/L2). HBM sees 8 B read and 4 B (plain) or 8 B (hi/lo) written per complex
+// sample.
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -98,6 +100,80 @@ __global__ void __launch_bounds__(32 * kWarps) k_to_planar(const float2 *__restr
                 out[at(2, q)] = make_uint2(h2u(lr01), h2u(lr23));
                 out[at(3, q)] = make_uint2(h2u(li01), h2u(li23));
             }
+        }
+    }
+}
+
+// The same conversion with the row held in registers: one CTA of 256 threads per
+// (channel, input) row, CPT consecutive spectra per thread (CPT = 8 or 16, rows of up
+// to 2048 or 4096 spectra), so the row is read from HBM once; the row maximum is a
+// block reduction. Each thread writes 8 or 16 FP16 values (16-byte pieces) per plane.
+template <int NPL, int CPT>
+__global__ void __launch_bounds__(256) k_to_planar_row(const float2 *__restrict__ X, __half *__restrict__ out,
+                                                       float *__restrict__ row_scale, int n_in, int K, int Kp) {
+    __shared__ float red[8];
+    const long long row = blockIdx.x;
+    const float2 *x = X + row * K;
+    const int s0 = threadIdx.x * CPT;
+    float2 v[CPT];
+    const bool vec = (K % 2) == 0;  // 16-byte aligned rows: pairs of spectra per load
+#pragma unroll
+    for (int e = 0; e < CPT; e += 2) {
+        const int s = s0 + e;
+        if (vec && s + 2 <= K) {
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(x + s));
+            v[e] = make_float2(q.x, q.y);
+            v[e + 1] = make_float2(q.z, q.w);
+        } else {
+            v[e] = s < K ? __ldg(x + s) : make_float2(0.f, 0.f);
+            v[e + 1] = s + 1 < K ? __ldg(x + s + 1) : make_float2(0.f, 0.f);
+        }
+    }
+    float m = 0.f;
+#pragma unroll
+    for (int e = 0; e < CPT; ++e) m = fmaxf(m, fmaxf(fabsf(v[e].x), fabsf(v[e].y)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+    int e2 = 0;
+    if (m > 0.f && m <= 3.4e38f) {
+        int k = 0;
+        frexpf(m, &k);
+        e2 = min(126, max(-126, 15 - k));
+    }
+    const float sc = ldexpf(1.0f, e2);
+    if (threadIdx.x == 0) row_scale[row] = ldexpf(1.0f, -e2);
+    if (s0 >= Kp) return;
+    const long long chan = row / n_in;
+    const int in = (int)(row - chan * n_in);
+    __half *base = out + ((chan * NPL) * n_in + in) * (long long)Kp + s0;
+    const long long plane = (long long)n_in * Kp;
+#pragma unroll
+    for (int e = 0; e < CPT; e += 8) {
+        if (s0 + e >= Kp) break;
+        uint32_t hr[4], hi[4], lr[4], li[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 a = make_float2(v[e + 2 * q].x * sc, v[e + 2 * q].y * sc);
+            const float2 b = make_float2(v[e + 2 * q + 1].x * sc, v[e + 2 * q + 1].y * sc);
+            const __half2 r = __floats2half2_rn(a.x, b.x), i = __floats2half2_rn(a.y, b.y);
+            hr[q] = h2u(r);
+            hi[q] = h2u(i);
+            if constexpr (NPL == 4) {
+                const float2 fr = __half22float2(r), fi = __half22float2(i);
+                lr[q] = h2u(__floats2half2_rn(a.x - fr.x, b.x - fr.y));
+                li[q] = h2u(__floats2half2_rn(a.y - fi.x, b.y - fi.y));
+            }
+        }
+        *reinterpret_cast<uint4 *>(base + e) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+        *reinterpret_cast<uint4 *>(base + plane + e) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        if constexpr (NPL == 4) {
+            *reinterpret_cast<uint4 *>(base + 2 * plane + e) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+            *reinterpret_cast<uint4 *>(base + 3 * plane + e) = make_uint4(li[0], li[1], li[2], li[3]);
         }
     }
 }
@@ -201,6 +277,16 @@ corr_status launch_to_planar(const Handle &h, const float2 *X, void *ws, int npl
     // 16-byte loads need every row start 16-byte aligned: K even and an aligned buffer
     const bool vec = (K % 2) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
     uint2 *out = static_cast<uint2 *>(ws);
+    if (Kp <= 4096 && n_rows <= 0x7fffffffLL && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+        // rows of up to 4096 spectra: held in registers, read once
+        __half *o = static_cast<__half *>(ws);
+        const unsigned nb = (unsigned)n_rows;
+        if (npl == 2 && Kp <= 2048) k_to_planar_row<2, 8><<<nb, 256, 0, st>>>(X, o, rsc, h.n_in, K, Kp);
+        else if (npl == 2) k_to_planar_row<2, 16><<<nb, 256, 0, st>>>(X, o, rsc, h.n_in, K, Kp);
+        else if (Kp <= 2048) k_to_planar_row<4, 8><<<nb, 256, 0, st>>>(X, o, rsc, h.n_in, K, Kp);
+        else k_to_planar_row<4, 16><<<nb, 256, 0, st>>>(X, o, rsc, h.n_in, K, Kp);
+        return check_launch("k_to_planar_row");
+    }
     if (npl == 2)
         launch_np<2>(vec, (unsigned)blocks, X, out, rsc, n_rows, h.n_in, K, Kp, st);
     else

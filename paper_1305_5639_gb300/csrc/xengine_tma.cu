@@ -45,6 +45,7 @@
 #include <cuda.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 #include "tc_ptx.cuh"
@@ -117,6 +118,12 @@ struct TParams {
     // also written as [block][chan][plane][B] int32 (plane 0 Re, 1 Im), st_nchan channels
     int *st_out;
     int st_kb, st_nchan;
+    // deferred integration dump run by the otherwise idle warps 2 and 3 of every CTA:
+    // side_dst[e] += side_src[e] for e < side_n (int2 for INT8, float2 for FP16), each
+    // CTA a contiguous slice; side_n = 0: none
+    const void *side_src;
+    double2 *side_dst;
+    long long side_n;
 };
 
 // Everything a role needs to know about one work item.
@@ -743,6 +750,54 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
         }
     }
 
+    if ((warp == 2 || warp == 3) && p.side_n > 0) {
+        // ------------------------------------------------------------ deferred dump
+        // The previous integration's accumulator into the FP64 long integration, in this
+        // CTA's slice, while the other roles run the X-engine: loads of 8 elements per
+        // thread in flight before their stores. The sums are exact (integer values below
+        // 2^53 for INT8; the FP64 add of the FP32 sums for FP16, as the dump kernel).
+        using AccT = typename std::conditional<MODE == kInt8, int2, float2>::type;
+        const AccT *src = static_cast<const AccT *>(p.side_src);
+        const long long lo = p.side_n * blockIdx.x / gridDim.x, hi = p.side_n * (blockIdx.x + 1) / gridDim.x;
+        constexpr int U = 8;
+        constexpr long long BATCH = 64 * U;  // elements per round of the 64 threads
+        constexpr int AHEAD = 4;              // rounds prefetched into L2 ahead of the loads
+        const int lt = threadIdx.x - 64;  // 0 .. 63
+        // bulk L2 prefetch of rounds [r0, r1) of both streams (one thread; 16-byte aligned
+        // ranges inside the buffers), so that the loads below hit L2
+        auto prefetch = [&](long long e_begin, long long e_end) {
+            e_begin = max(e_begin, lo);
+            e_end = min(e_end, hi);
+            if (e_end <= e_begin) return;
+            const uintptr_t sa = reinterpret_cast<uintptr_t>(src + e_begin) & ~(uintptr_t)15;
+            const uintptr_t se = reinterpret_cast<uintptr_t>(src + e_end) & ~(uintptr_t)15;
+            const uintptr_t da = reinterpret_cast<uintptr_t>(p.side_dst + e_begin);
+            const uintptr_t de = reinterpret_cast<uintptr_t>(p.side_dst + e_end);
+            if (se > sa) tc::prefetch_l2_bulk(reinterpret_cast<const void *>(sa), (uint32_t)(se - sa));
+            tc::prefetch_l2_bulk(reinterpret_cast<const void *>(da), (uint32_t)(de - da));
+        };
+        if (lt == 0) prefetch(lo, lo + AHEAD * BATCH);
+        for (long long e0 = lo + lt; e0 < hi; e0 += BATCH) {
+            if (*abort_flag) break;
+            if (lt == 0) prefetch(e0 + AHEAD * BATCH, e0 + (AHEAD + 1) * BATCH);
+            AccT a[U];
+            double2 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long e = e0 + 64 * u;
+                if (e < hi) {
+                    a[u] = __ldcs(src + e);
+                    v[u] = __ldcg(p.side_dst + e);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long e = e0 + 64 * u;
+                if (e < hi) p.side_dst[e] = make_double2(v[u].x + (double)a[u].x, v[u].y + (double)a[u].y);
+            }
+        }
+    }
+
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -872,6 +927,12 @@ corr_status launch_xengine_tma_range(const Handle &h, const void *planes, int np
     p.vis64 = (h.flags & CORR_FLAG_FUSED_DUMP) ? h.vis64 : nullptr;
     p.gains = gains;
     p.rsc = row_scale;
+    if (h.dump_pending) {
+        // the previous integration's deferred dump rides along (all channels, one launch)
+        p.side_dst = h.vis64;
+        p.side_src = h.pending_src;
+        p.side_n = (long long)h.n_chan * h.n_base;
+    }
     p.status = h.status;
     p.B = h.n_base;
     const int nb = (h.n_in + TILE - 1) / TILE;
