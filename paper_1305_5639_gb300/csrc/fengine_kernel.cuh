@@ -176,6 +176,10 @@ __global__ void __launch_bounds__(kThreads, (N >= 2048 || (MODE == kPower && N >
     using C = FCfg<N, I8, MODE>;
     constexpr int T1 = C::T1, T2 = C::T2, TG = C::TG, G = C::G, EXS = C::EXS, SB = C::SB, ROWW = C::ROWW;
     constexpr int TV = T1 > T2 ? T1 : T2;  // register values per thread
+    // square 32- or 64-point passes read the exchange into float arrays and do pass 2's
+    // first stage in scalar arithmetic (no register moves into the (re, im) pairs); the
+    // smaller lengths keep the in-place reads, which fit their register budgets
+    constexpr bool kScalarStage = T1 == T2 && T2 >= 32;
     constexpr bool DLY = FEAT == kDelay;  // delay code compiled in
     // int8 samples enter the plain FFT scaled by 256 on an offset (i8_to_f2_scaled); the
     // delay instantiation converts them exactly (measured faster there)
@@ -329,30 +333,71 @@ __global__ void __launch_bounds__(kThreads, (N >= 2048 || (MODE == kPower && N >
                 exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T1))].x;
             });
         group_sync();
-        if (act2) {
+        if constexpr (kScalarStage) {
+            // the rows are read into plain float arrays (a 16-byte load fills four
+            // consecutive registers, which the (re, im) register pairs of v cannot offer)
+            float rin[T2], iin[T2];
+            if (act2) {
 #pragma unroll
-            for (int j = 0; j < T2 / 4; ++j) {
-                const float4 r = exrow[j];
-                v[4 * j].x = r.x, v[4 * j + 1].x = r.y, v[4 * j + 2].x = r.z, v[4 * j + 3].x = r.w;
+                for (int j = 0; j < T2 / 4; ++j) {
+                    const float4 r = exrow[j];
+                    rin[4 * j] = r.x, rin[4 * j + 1] = r.y, rin[4 * j + 2] = r.z, rin[4 * j + 3] = r.w;
+                }
             }
-        }
-        group_sync();
-        if (act1)
-            sfor<0, T1>([&](auto K1) {
-                constexpr int k1 = decltype(K1)::value;
-                exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T1))].y;
+            group_sync();
+            if (act1)
+                sfor<0, T1>([&](auto K1) {
+                    constexpr int k1 = decltype(K1)::value;
+                    exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T1))].y;
+                });
+            group_sync();
+            if (act2) {
+#pragma unroll
+                for (int j = 0; j < T2 / 4; ++j) {
+                    const float4 r = exrow[j];
+                    iin[4 * j] = r.x, iin[4 * j + 1] = r.y, iin[4 * j + 2] = r.z, iin[4 * j + 3] = r.w;
+                }
+            }
+            group_sync();
+            if (use_async && s0 + G < SB) issue_raw(s0 + G + g);  // next frame into the free buffer
+            // pass 2: its first radix-2 stage in scalar arithmetic, from the float arrays
+            // into the (re, im) pairs, then the remaining stages on the pairs
+            sfor<0, T2 / 2>([&](auto J) {
+                constexpr int a = decltype(J)::value, b = a + T2 / 2;
+                const float ar = rin[a], ai = iin[a], br = rin[b], bi = iin[b];
+                v[a] = make_float2(ar + br, ai + bi);
+                if constexpr (4 * a == T2)
+                    v[b] = make_float2(ai - bi, br - ar);  // (x - y)(-j)
+                else
+                    v[b] = mul_w<a, T2>(make_float2(ar - br, ai - bi));
             });
-        group_sync();
-        if (act2) {
+            fft_dif<T2, TV, 1>(v);  // v[bitrev(k2)] = X[t + T1 k2]
+        } else {
+            if (act2) {
 #pragma unroll
-            for (int j = 0; j < T2 / 4; ++j) {
-                const float4 r = exrow[j];
-                v[4 * j].y = r.x, v[4 * j + 1].y = r.y, v[4 * j + 2].y = r.z, v[4 * j + 3].y = r.w;
+                for (int j = 0; j < T2 / 4; ++j) {
+                    const float4 r = exrow[j];
+                    v[4 * j].x = r.x, v[4 * j + 1].x = r.y, v[4 * j + 2].x = r.z, v[4 * j + 3].x = r.w;
+                }
             }
+            group_sync();
+            if (act1)
+                sfor<0, T1>([&](auto K1) {
+                    constexpr int k1 = decltype(K1)::value;
+                    exg[k1 * EXS + t] = v[bitrev(k1, ilog2(T1))].y;
+                });
+            group_sync();
+            if (act2) {
+#pragma unroll
+                for (int j = 0; j < T2 / 4; ++j) {
+                    const float4 r = exrow[j];
+                    v[4 * j].y = r.x, v[4 * j + 1].y = r.y, v[4 * j + 2].y = r.z, v[4 * j + 3].y = r.w;
+                }
+            }
+            group_sync();
+            if (use_async && s0 + G < SB) issue_raw(s0 + G + g);  // next frame into the free buffer
+            fft_dif<T2>(v);  // v[bitrev(k2)] = X[t + T1 k2]
         }
-        group_sync();
-        if (use_async && s0 + G < SB) issue_raw(s0 + G + g);  // next frame into the free buffer
-        fft_dif<T2>(v);  // v[bitrev(k2)] = X[t + T1 k2]
         if (valid && act2) {
             sfor<0, T2>([&](auto K2) {
                 constexpr int k2 = decltype(K2)::value;

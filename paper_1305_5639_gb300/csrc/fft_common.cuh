@@ -135,12 +135,14 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 
 // In-register P-point DFT (Eq. 1 on P points) of v[0 .. P-1], radix-2 decimation in
-// frequency (v may hold more than P values). On return v[bitrev(k)] holds X[k].
-template <int P, int L>
+// frequency (v may hold more than P values), from stage S0 on (S0 = 0: the whole
+// transform; S0 = 1 when the caller has done the first stage). On return v[bitrev(k)]
+// holds X[k].
+template <int P, int L, int S0 = 0>
 __device__ __forceinline__ void fft_dif(float2 (&v)[L]) {
     static_assert(P <= L, "DFT longer than the register array");
     constexpr int LG = ilog2(P);
-    sfor<0, LG>([&](auto S) {
+    sfor<S0, LG>([&](auto S) {
         constexpr int half = P >> (decltype(S)::value + 1);
         constexpr int len = 2 * half;
         sfor<0, P / len>([&](auto Bk) {
