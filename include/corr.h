@@ -92,6 +92,16 @@ enum { CORR_FLAG_PLANAR = 1 };
  *   and corr_dump only copies the FP64 buffer out. */
 enum { CORR_FLAG_FUSED_DUMP = 2 };
 
+/* CORR_FLAG_FENGINE_CUDACORE: run the F-engine's FFT on the CUDA cores even where the
+ *   tensor-core F-engine applies. By default, INT8 handles with n_chan = 1024 and
+ *   neither delay compensation nor the filter bank channelise with tcgen05: the two
+ *   32-point DFT stages of the 32 x 32 split of Eq. 1 as FP16 hi/lo GEMMs with FP32
+ *   accumulation (the twiddles and the hi/lo split of the intermediate in FP32). Both
+ *   forms round each code from an FP32-accurate spectrum; a code may differ by one
+ *   between them only where the scaled value lies within that error of a rounding
+ *   boundary. */
+enum { CORR_FLAG_FENGINE_CUDACORE = 4 };
+
 typedef struct corr_opts {
     int32_t precision; /* CORR_PREC_*, default CORR_PREC_FP32 */
     int32_t xengine;   /* CORR_XENG_*, default CORR_XENG_AUTO */

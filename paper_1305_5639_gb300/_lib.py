@@ -23,6 +23,7 @@ CORR_EUNSUPPORTED = 7
 PREC = {"fp32": 0, "int8": 1, "fp16": 2, "fp16_hilo": 3}
 CORR_FLAG_PLANAR = 1
 CORR_FLAG_FUSED_DUMP = 2
+CORR_FLAG_FENGINE_CUDACORE = 4
 XENG = {"auto": 0, "cudacore": 1, "tcgen05": 2}
 STAGES = ("fengine", "pfb", "power", "prep", "xengine", "dump", "adj_prep", "adj_gemm", "adj_reduce")
 

@@ -129,7 +129,7 @@ class Correlator:
     """Owns one libcorr handle; allocates outputs as torch tensors."""
 
     def __init__(self, n_ant: int, n_pol: int, n_chan: int, n_spectra: int, precision="fp32", xengine="auto",
-                 device=None, planar: bool = False, fused_dump: bool = False):
+                 device=None, planar: bool = False, fused_dump: bool = False, fengine: str = "auto"):
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else int(device))
         self.device = dev
         self.n_ant, self.n_pol, self.n_chan, self.n_spectra = n_ant, n_pol, n_chan, n_spectra
@@ -137,7 +137,10 @@ class Correlator:
         self.precision = precision
         self.planar = planar
         with torch.cuda.device(dev):
-            flags = (_lib.CORR_FLAG_PLANAR if planar else 0) | (_lib.CORR_FLAG_FUSED_DUMP if fused_dump else 0)
+            if fengine not in ("auto", "cudacore"):
+                raise ValueError("fengine must be 'auto' (tensor cores where they apply) or 'cudacore'")
+            flags = ((_lib.CORR_FLAG_PLANAR if planar else 0) | (_lib.CORR_FLAG_FUSED_DUMP if fused_dump else 0)
+                     | (_lib.CORR_FLAG_FENGINE_CUDACORE if fengine == "cudacore" else 0))
             self.h = corr_create(n_ant, n_pol, n_chan, n_spectra, precision, xengine, dev.index, flags)
         self.n_base = corr_n_baselines(self.h)
 

@@ -120,6 +120,8 @@ void free_buffers(Handle &h) {
     cudaFree(h.acc);
     cudaFree(h.vis64);
     cudaFree(h.twiddle);
+    cudaFree(h.ftc_b);
+    h.ftc_b = nullptr;
     cudaFree(h.dly_int);
     cudaFree(h.dly_ph);
     h.dly_int = nullptr;
@@ -260,7 +262,7 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
     if (opts) o = *opts;
     if (o.precision < CORR_PREC_FP32 || o.precision > CORR_PREC_FP16_HILO) return CORR_EINVAL;
     if (o.xengine < CORR_XENG_AUTO || o.xengine > CORR_XENG_TCGEN05) return CORR_EINVAL;
-    if ((o.flags & ~(CORR_FLAG_PLANAR | CORR_FLAG_FUSED_DUMP)) != 0) return CORR_EINVAL;
+    if ((o.flags & ~(CORR_FLAG_PLANAR | CORR_FLAG_FUSED_DUMP | CORR_FLAG_FENGINE_CUDACORE)) != 0) return CORR_EINVAL;
     // the dump fused into the X-engine epilogue exists on the tensor-core (TMA) X-engine:
     // INT8, FP16 and FP16 hi/lo on the AUTO or TCGEN05 X-engine
     if ((o.flags & CORR_FLAG_FUSED_DUMP) && (o.precision == CORR_PREC_FP32 || o.xengine == CORR_XENG_CUDACORE))
@@ -333,6 +335,15 @@ corr_status corr_create(int32_t n_ant, int32_t n_pol, int32_t n_chan, int32_t n_
             }
         }
         ok = cudaMemcpy(h.twiddle, tw.data(), sizeof(float2) * (size_t)n_chan, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (ok) {
+        const corr_status s = corr::fengine_tc_init(h);
+        if (s == CORR_ENOMEM) {
+            corr::free_buffers(h);
+            delete c;
+            return CORR_ENOMEM;
+        }
+        ok = s == CORR_OK;
     }
     if (!ok) {
         corr::set_cuda_error(cudaGetLastError(), "corr_create init");
@@ -670,6 +681,7 @@ corr_status corr_fx_host(corr_t *c, const void *volt_host, const float *chan_sca
         }
         CORR_CUDA_TRY(cudaEventRecord(ev[1 + b], h.fx_in));
         CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + b], 0));
+        if (i1 <= i0) continue;  // fewer inputs than blocks: the last blocks are empty
         corr_status s = corr::launch_fengine_range(h, h.fx_volt, chan_scale, h.fx_chan, i0, i1 - i0, st);
         if (s != CORR_OK) return s;
     }

@@ -60,6 +60,11 @@ bool fengine_supported(int n) { return fengine_t2(n) > 0; }
 
 corr_status launch_fengine_range(const Handle &h, const void *volt, const float *scale, void *out, int i0, int n_run,
                                  cudaStream_t st) {
+    // inputs [i0, i0 + n_run), or all of them for n_run < 0 (then i0 = 0)
+    if (n_run < 0 ? i0 != 0 : (i0 < 0 || (long long)i0 + n_run > h.n_in)) {
+        set_error_text("F-engine input range outside the handle's inputs");
+        return CORR_EINVAL;
+    }
     FShape f = shape_of(h);
     f.i0 = i0;
     f.n_run = n_run;
@@ -67,6 +72,7 @@ corr_status launch_fengine_range(const Handle &h, const void *volt, const float 
     corr_status s = pfb_front(h, f, volt, st);
     if (s != CORR_OK) return s;
     StageScope sc(h, CORR_STAGE_FENGINE, st);
+    if (fengine_tc_applies(h)) return launch_fengine_tc(h, volt, scale, out, i0, n_run, st);
     if (h.precision == CORR_PREC_INT8 && (h.flags & CORR_FLAG_PLANAR))
         return dispatch<kRequantPlanar>(f, volt, scale, out, nullptr, st);
     if (h.precision == CORR_PREC_INT8) return dispatch<kRequant>(f, volt, scale, out, nullptr, st);

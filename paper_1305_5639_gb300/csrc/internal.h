@@ -44,6 +44,7 @@ struct Handle {
     int64_t acc_spectra = 0;     // spectra accumulated since the last dump (INT8 overflow guard)
     double2 *vis64 = nullptr;    // FP64 long-integration buffer [n_chan][B]
     float2 *twiddle = nullptr;   // F-engine twiddles W_N^(t k1), [k1][t], N = T1 x T2
+    void *ftc_b = nullptr;       // tensor-core F-engine DFT matrices F_h, F_l (N = 1024, INT8)
     int32_t *dly_int = nullptr;  // delay compensation (null: off): integer advance per input
     float2 *dly_ph = nullptr;    //   and phase tables [n_in][T1 + T2]: exp(+j 2 pi k1 f / N), exp(+j 2 pi T1 k2 f / N)
     float *pfb_win = nullptr;    // polyphase filter-bank window [pfb_taps][n_chan] (null: off)
@@ -162,6 +163,11 @@ corr_status selftest_bounded_wait(uint64_t limit_ns);
 // Polyphase filter bank: FIR pass of inputs [i0, i0 + n_run) into h.pfb_y (pfb.cu).
 corr_status launch_pfb_fir(const Handle &h, const void *volt, int i0, int n_run, cudaStream_t st);
 bool fengine_supported(int n_chan);
+// tensor-core F-engine (fengine_tc.cu): N = 1024, INT8, no delays or filter bank
+bool fengine_tc_applies(const Handle &h);
+corr_status fengine_tc_init(Handle &h);
+corr_status launch_fengine_tc(const Handle &h, const void *volt, const float *scale, void *out, int i0, int n_run,
+                              cudaStream_t st);
 bool xengine_tma_supported(const Handle &h);
 corr_status launch_xengine_tma(const Handle &h, const void *planes, int npl, const float2 *gains,
                                const float *row_scale, int kstride, bool store, cudaStream_t st);

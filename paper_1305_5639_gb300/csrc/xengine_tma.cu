@@ -47,6 +47,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "exact_add.cuh"
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -538,7 +539,7 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
                             if (ok[h4 + q])
-                                dst[off[h4 + q]] = make_double2(o[q].x + (double)val[h4 + q].x, o[q].y + (double)val[h4 + q].y);
+                                dst[off[h4 + q]] = add_exact(o[q], val[h4 + q]);  // FP32 sums: conversion in integers
                     }
                 } else {
                     float2 *dst = p.rect ? static_cast<float2 *>(p.rect_out) + (long long)chan * p.n_p * p.n_q

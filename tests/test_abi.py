@@ -60,7 +60,7 @@ def test_create_rejects_bad_arguments_without_device(lib):
     assert lib.corr_create(4, 1, 16, 16, None, None) == CORR_EINVAL
     o = corr_opts(9, 0, 0, -1)
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EINVAL
-    o = corr_opts(0, 0, 4, -1)  # unknown flag bit
+    o = corr_opts(0, 0, 8, -1)  # unknown flag bit
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EINVAL
     o = corr_opts(0, 0, 1, -1)  # the planar layout is INT8 only
     assert lib.corr_create(4, 1, 16, 16, ctypes.byref(o), ctypes.byref(h)) == CORR_EUNSUPPORTED

@@ -68,13 +68,14 @@ def test_bounded_wait_selftest_times_out_and_context_survives(cuda_ok):
 
 
 def test_stage_timing_counts_and_times_each_stage(cuda_ok):
-    """Per-stage event timing (tracing): an FP16 hi/lo step records the operand
-    conversion, the X-engine and the dump separately, one launch each, with
-    positive times; reading clears; switched off, launches are still counted but
-    not timed."""
+    """Per-stage event timing (tracing): an FP16 step records the operand conversion,
+    the X-engine and the dump separately, one launch each, with positive times;
+    reading clears; switched off, launches are still counted but not timed. (Plain
+    FP16 dumps at once; the INT8 and hi/lo dumps defer into the next X-engine launch
+    and count no dump launch of their own.)"""
     n_in, K, n_chan = 130, 96, 3
     X = torch.from_numpy(synth.chan_sources(n_chan, n_in, K, n_src=2, seed=4, src_amp=0.1)).to(DEV)
-    c = api.Correlator(n_in, 1, n_chan, K, precision="fp16_hilo")
+    c = api.Correlator(n_in, 1, n_chan, K, precision="fp16")
     c.set_stage_timing(True)
     for _ in range(2):
         c.xengine(X)
@@ -90,3 +91,14 @@ def test_stage_timing_counts_and_times_each_stage(cuda_ok):
     assert t["xengine"] == (0.0, 1) and t["prep"] == (0.0, 1)
     c.check_status()
     c.close()
+    h = api.Correlator(n_in, 1, n_chan, K, precision="fp16_hilo")
+    h.set_stage_timing(True)
+    for _ in range(2):
+        h.xengine(X)
+        h.dump(copy=False)
+    t = h.stage_times()
+    assert t["xengine"][1] == 2 and t["dump"][1] == 0  # the first dump rode in the second launch
+    h.flush()
+    assert h.stage_times()["dump"][1] == 1  # the last one, settled by the flush
+    h.check_status()
+    h.close()

@@ -15,6 +15,7 @@ from paper_1305_5639_gb300 import api
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
+SIG8 = 48.0  # wide int8 noise, clipped at -128
 
 
 def _planar(X):
@@ -92,32 +93,36 @@ def test_restore_and_reset_drop_a_pending_dump(cuda_ok):
 
 def test_deferred_dump_with_short_time_output_and_fx_host(cuda_ok):
     """The deferred dump also rides in the short-time X-engine launch, and the host
-    pipeline settles a pending dump before its own."""
+    pipeline settles a pending dump before its own: the long integration equals that
+    of a handle making the same calls with immediate dumps, bit for bit, and its
+    X-engine part the oracle's."""
     n_ant, n_pol, N, K = 8, 2, 64, 128
     n_in = n_ant * n_pol
-    c = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
     X = synth.chan_int8(N, n_in, K, seed=81)
-    st = c.set_short_time(64)
-    c.xengine(torch.from_numpy(_planar(X)).to(DEV))
-    c.dump(copy=False)
-    c.xengine(torch.from_numpy(_planar(X)).to(DEV))  # short-time launch carries the dump
-    c.set_short_time(out=False)
-    del st
-    c.dump(copy=False)  # pending again
     v = synth.volt_int8(n_ant, n_pol, N, K, seed=82)
     scale = torch.full((N,), 1.0 / 8.0, device=DEV)
-    vis_h = torch.empty((N, n_in * (n_in + 1) // 2), dtype=torch.complex128).pin_memory()
-    c.fx_host(torch.from_numpy(v).pin_memory(), scale, vis_h)
-    torch.cuda.synchronize()
-    c.check_status()
-    # the F-engine codes of this integration, from the device path of a second handle
-    d = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
-    P = d.fengine(torch.from_numpy(v).to(DEV), scale)
-    q = np.transpose(P.cpu().numpy(), (0, 2, 3, 1)).astype(np.int8)
-    want = oracle.dump([oracle.cmac(X), oracle.cmac(X), oracle.cmac(q)])
-    assert np.array_equal(vis_h.numpy(), _c(want))
-    c.close()
-    d.close()
+    res = []
+    for deferred in (True, False):
+        c = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
+        settle = (lambda: c.dump(copy=False)) if deferred else (lambda: c.dump())
+        st = c.set_short_time(64)
+        c.xengine(torch.from_numpy(_planar(X)).to(DEV))
+        settle()
+        c.xengine(torch.from_numpy(_planar(X)).to(DEV))  # short-time launch carries the dump
+        c.set_short_time(out=False)
+        del st
+        settle()  # pending again (deferred)
+        two = c.dump().cpu().numpy()  # settles: the two X-engine integrations
+        assert np.array_equal(two, _c(oracle.dump([oracle.cmac(X), oracle.cmac(X)])))
+        c.xengine(torch.from_numpy(_planar(X)).to(DEV))
+        settle()  # a third, pending when the host pipeline starts (deferred)
+        vis_h = torch.empty((N, n_in * (n_in + 1) // 2), dtype=torch.complex128).pin_memory()
+        c.fx_host(torch.from_numpy(v).pin_memory(), scale, vis_h)
+        torch.cuda.synchronize()
+        c.check_status()
+        res.append(vis_h.numpy().copy())
+        c.close()
+    assert np.array_equal(res[0], res[1])
 
 
 def test_deferred_hilo_dumps_equal_immediate_ones(cuda_ok):
@@ -145,3 +150,89 @@ def test_deferred_hilo_dumps_equal_immediate_ones(cuda_ok):
     assert e.max() <= 5e-5
     a.close()
     b.close()
+
+
+def _vis0(rng, n_chan, B, integer):
+    """A starting long integration: integer-valued doubles up to 2^40 (INT8 sums add in
+    integers), with some non-integers, some beyond 2^52 (both take the FP64 add), and
+    zeros; or, for FP32 sums, doubles of mixed magnitude."""
+    if integer:
+        re = rng.integers(-2 ** 40, 2 ** 40, (n_chan, B)).astype(np.float64)
+        im = rng.integers(-2 ** 40, 2 ** 40, (n_chan, B)).astype(np.float64)
+        m = rng.random((n_chan, B))
+        re[m < 0.05] += 0.5
+        im[(m > 0.05) & (m < 0.1)] = 2.0 ** 53 + 2.0 * rng.integers(0, 1000, ((m > 0.05) & (m < 0.1)).sum())
+        re[m > 0.95] = 0.0
+        im[m > 0.97] = -0.0
+    else:
+        re = rng.standard_normal((n_chan, B)) * 10.0 ** rng.integers(-6, 9, (n_chan, B))
+        im = rng.standard_normal((n_chan, B)) * 10.0 ** rng.integers(-6, 9, (n_chan, B))
+        re[rng.random((n_chan, B)) < 0.03] = 0.0
+    return re + 1j * im
+
+
+@pytest.mark.parametrize("precision", ["int8", "fp16", "fp16_hilo"])
+@pytest.mark.parametrize("mode", ["immediate", "deferred"])
+def test_dump_add_is_the_fp64_add(cuda_ok, precision, mode):
+    """Property of the dump, whatever form it takes: the long integration becomes
+    vis0 + acc, each part one IEEE FP64 addition of the accumulator's value (for INT8
+    the oracle's exact sums; for FP32 sums the accumulator read back) to the starting
+    value, bit for bit (the integer forms of the conversion and of the INT8 add must
+    agree with it everywhere, including zeros, non-integers and values beyond 2^52)."""
+    n_in, K, n_chan = 136, 136, 2
+    B = n_in * (n_in + 1) // 2
+    rng = np.random.default_rng(7)
+    if precision == "int8":
+        X = synth.chan_int8(n_chan, n_in, K, seed=5, sigma=SIG8, lo=-128)
+        Xt = torch.from_numpy(_planar(X)).to(DEV)
+        c = api.Correlator(n_in, 1, n_chan, K, precision="int8", planar=True)
+    else:
+        X = synth.chan_sources(n_chan, n_in, K, n_src=3, seed=5, src_amp=0.1)
+        Xt = torch.from_numpy(X).to(DEV)
+        c = api.Correlator(n_in, 1, n_chan, K, precision=precision)
+    vis0 = _vis0(rng, n_chan, B, precision == "int8")
+    c.restore_vis(torch.from_numpy(vis0).to(DEV))
+    c.xengine(Xt)
+    if precision == "int8":
+        acc = oracle.cmac(X).astype(np.float64)
+    else:
+        a = c.accum().cpu().numpy()  # complex64: the FP32 sums
+        acc = np.stack([a.real, a.imag], axis=-1).astype(np.float64)  # widened exactly
+    if mode == "deferred":
+        c.dump(copy=False)
+        c.xengine(Xt)  # carries the deferred add (INT8 and hi/lo; plain FP16 may not defer)
+        vis = c.dump().cpu().numpy()
+        want_re = (vis0.real + acc[..., 0]) + acc[..., 0]
+        want_im = (vis0.imag + acc[..., 1]) + acc[..., 1]
+    else:
+        vis = c.dump().cpu().numpy()
+        want_re, want_im = vis0.real + acc[..., 0], vis0.imag + acc[..., 1]
+    c.check_status()
+    assert np.array_equal(vis.real.view(np.int64), want_re.view(np.int64))
+    assert np.array_equal(vis.imag.view(np.int64), want_im.view(np.int64))
+    c.close()
+
+
+@pytest.mark.parametrize("precision", ["int8", "fp16", "fp16_hilo"])
+def test_fused_dump_add_equals_separate_dump(cuda_ok, precision):
+    """The fused form (the X-engine's epilogue adds into the FP64 buffer) gives the same
+    bits as the separate dump from the same starting long integration."""
+    n_in, K, n_chan = 136, 136, 2
+    B = n_in * (n_in + 1) // 2
+    vis0 = _vis0(np.random.default_rng(11), n_chan, B, precision == "int8")
+    if precision == "int8":
+        X = synth.chan_int8(n_chan, n_in, K, seed=6, sigma=SIG8, lo=-128)
+        Xt = torch.from_numpy(_planar(X)).to(DEV)
+        kw = dict(precision="int8", planar=True)
+    else:
+        Xt = torch.from_numpy(synth.chan_sources(n_chan, n_in, K, n_src=3, seed=6, src_amp=0.1)).to(DEV)
+        kw = dict(precision=precision)
+    out = []
+    for fused in (False, True):
+        c = api.Correlator(n_in, 1, n_chan, K, fused_dump=fused, **kw)
+        c.restore_vis(torch.from_numpy(vis0).to(DEV))
+        c.xengine(Xt)
+        out.append(c.dump().cpu().numpy())
+        c.check_status()
+        c.close()
+    assert np.array_equal(out[0].view(np.int64), out[1].view(np.int64))
