@@ -19,7 +19,9 @@
 // item is four groups of four frames; a group is one 128-row tile: rows (frame, t) in
 // stage 1 and (frame, k1) in stage 2, columns (k, Re / Im) interleaved; the hi/lo
 // products of a stage accumulate into the same 64 TMEM columns, and the accumulators
-// are four deep, so the MMAs run up to four groups ahead of the drains.
+// are four deep, so the MMAs run up to four groups ahead of the drains. Within a
+// frame, stage 1's rows are ordered so that the converters' 16-byte stores are free of
+// bank conflicts: row 16 e + u holds t = 2 u + e.
 // Warp roles:
 //   warp 0       issues the MMAs (one thread) and owns the TMEM allocation
 //   warps 1-2    convert the raw frames (bulk-copied into a 4-slot ring) into stage 1's
@@ -263,9 +265,9 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fengine_tc(const FtParams p) 
             uint32_t w[kFtR];
 #pragma unroll
             for (int m = 0; m < kFtR; ++m) w[m] = valid ? lds_u32(rs + 2 * kFtR * m) : 0u;
-            // rows (q, 2u) and (q, 2u + 1) of stage 1's A tile: columns (m, Re / Im), 16-byte
-            // chunks of 4 m
-            const int r0 = 32 * q + 2 * u;
+            // rows of t = 2u and t = 2u + 1 (tile rows 32 q + u and 32 q + 16 + u): columns
+            // (m, Re / Im), 16-byte chunks of 4 m
+            const int r0 = 32 * q + u;
 #pragma unroll
             for (int kc = 0; kc < 8; ++kc) {
                 uint4 va, vb;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fengine_tc(const FtParams p) 
                 i8x2_to_h2(w[4 * kc + 2], va.z, vb.z);
                 i8x2_to_h2(w[4 * kc + 3], va.w, vb.w);
                 sts_v4(atile + sw128_off(r0, 8 * kc), va);
-                sts_v4(atile + sw128_off(r0 + 1, 8 * kc), vb);
+                sts_v4(atile + sw128_off(r0 + 16, 8 * kc), vb);
             }
             tc::fence_proxy_async_smem();
             __syncwarp();
@@ -342,11 +344,12 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fengine_tc(const FtParams p) 
         }
     } else if (warp <= 11) {
         // ------------------------------------------------------------ stage-1 drain
-        const int q = warp & 3;           // TMEM lane quarter = frame of the group; lane = t
-        const int kh = (warp - 4) >> 2;   // k1 in [16 kh, 16 kh + 16)
-        float2 tw[16];                    // W_1024^(t k1) of this lane's t
+        const int q = warp & 3;                      // TMEM lane quarter = frame of the group
+        const int kh = (warp - 4) >> 2;              // k1 in [16 kh, 16 kh + 16)
+        const int t = 2 * (lane & 15) + (lane >> 4);  // this lane's row holds t (stage-1 row order)
+        float2 tw[16];                               // W_1024^(t k1)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) tw[j] = __ldg(p.tw + (16 * kh + j) * kFtR + lane);
+        for (int j = 0; j < 16; ++j) tw[j] = __ldg(p.tw + (16 * kh + j) * kFtR + t);
         for (int gs = 0; gs < total; ++gs) {
             const int b = gs & 1, c = gs & 3;
             const uint32_t ph = (uint32_t)((gs >> 1) & 1);
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fengine_tc(const FtParams p) 
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 // row (q, k1) of stage 2's A tiles, column pair (t, Re / Im)
-                const uint32_t off = sw128_off(32 * q + 16 * kh + j, 2 * lane);
+                const uint32_t off = sw128_off(32 * q + 16 * kh + j, 2 * t);
                 sts_u32(ah + off, yh[2 * j]);
                 sts_u32(al + off, yh[2 * j + 1]);
             }
