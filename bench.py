@@ -256,7 +256,9 @@ def run_ours(args):
     planar = args.layout == "planar"
     fused = args.fused_dump
     corr = api.Correlator(n_ant, n_pol, N, K, precision="int8", xengine=args.xengine, planar=planar,
-                          fused_dump=fused)
+                          fused_dump=fused, fengine=args.fengine)
+    # the tensor-core F-engine runs for 1024 channels without delays or a filter bank
+    f_tc = args.fengine == "auto" and N == 1024 and not args.pfb and not args.delays
     chan = corr.chan_buffer()
     if args.pfb > 0:
         # polyphase filter bank: a Hann-windowed sinc of args.pfb taps
@@ -446,12 +448,14 @@ def run_ours(args):
     if args.xengine == "cudacore":
         roof_x = {"bound": "alu", "achieved": x_ach, "peak": None, "unit": "TOP/s", "frac": None,
                   "traffic": None, "kernel": "k_xeng_i8 (CUDA-core dp4a)"}
-    f_traffic = _traffic("k_fengine") if (full_size and planar and not args.pfb and not args.delays) else None
+    f_kernel = "k_fengine_tc" if f_tc else "k_fengine"
+    f_traffic = _traffic(f_kernel) if (full_size and planar and not args.pfb and not args.delays) else None
     roof_f = {"bound": "hbm", "achieved": f_ach, "peak": peaks["hbm"], "unit": "GB/s", "frac": f_ach / peaks["hbm"],
               "traffic": f_traffic,
               "traffic_ratio": None if f_traffic is None else f_traffic / f_bytes,
               "layout_bytes": f_layout_bytes,
-              "kernel": "k_fengine (FFT + int8 re-packing + corner turn)",
+              "kernel": ("k_fengine_tc (32 x 32 FFT: both DFT stages as FP16 hi/lo GEMMs on tcgen05, int8 "
+                         "re-packing, corner turn)" if f_tc else "k_fengine (FFT + int8 re-packing + corner turn)"),
               "peak_note": f"{peaks['src']} HBM copy bandwidth",
               "algorithmic": f"{f_bytes:.4g} bytes per launch (read 2 B + write 2 B per complex sample); the "
                              f"{args.layout} exchange layout moves {f_layout_bytes:.4g}"}
@@ -477,7 +481,7 @@ def run_ours(args):
         configs = {}
         runners = {"A": lambda: bench_A(10, 3, dev, peaks, mhz),
                    "C": lambda: bench_C(2, 1, dev, peaks, args.c_window),
-                   "D": lambda: bench_D(10, 3, dev, peaks, bool(args.comparator)),
+                   "D": lambda: bench_D(10, 3, dev, peaks, bool(args.comparator), args.d_window),
                    "E": lambda: bench_E(10, 3, dev, peaks, args.e_window)}
         for name in args.configs:
             configs[name] = runners[name]()
@@ -778,17 +782,18 @@ def bench_C(steps, warmup, dev, peaks, window):
     return out
 
 
-def bench_D(steps, warmup, dev, peaks, comparator=True):
+def bench_D(steps, warmup, dev, peaks, comparator=True, window=1024):
     """Calibration workload: 512 inputs, 1024 channels, 1024 spectra, complex64,
     per-input complex gains; one gained forward X-engine (hi/lo, tensor cores) and
     one adjoint (dL/dX, dL/dg on tensor cores) per step. The FP32 CUDA-core forward
-    and adjoint run once beside it; the gradients are compared with each other."""
+    and adjoint run once beside it; the gradients are compared with each other.
+    `window` < 1024 runs that many of the channels (profiler captures)."""
     import torch
 
     import synth
     from paper_1305_5639_gb300 import api
 
-    n_in, N, K = 512, 1024, 1024
+    n_in, N, K = 512, window, 1024
     B = n_in * (n_in + 1) // 2
     gen = torch.Generator(device=dev).manual_seed(0)
     X = torch.complex(torch.randn((N, n_in, K), generator=gen, device=dev),
@@ -836,8 +841,8 @@ def bench_D(steps, warmup, dev, peaks, comparator=True):
     gemm_ms = st["adj_gemm"][0] / steps
     ach = 8.0 * cm_b / (gemm_ms * 1e-3) / 1e12
     out = {
-        "workload": "calibration: 512 inputs, 1024 channels, 1024 spectra, complex64, per-input gains; gained "
-                    "X-engine + adjoint (dL/dX, dL/dg)",
+        "workload": f"calibration: 512 inputs, {N} of 1024 channels, 1024 spectra, complex64, per-input gains; "
+                    "gained X-engine + adjoint (dL/dX, dL/dg)",
         "ms_per_step": ms, "cmac_per_s": (cm_f + cm_b) / (ms * 1e-3),
         "forward_ms": tc["forward"], "backward_ms": tc["backward"],
         "stages_ms": _stage_ms(st, steps), "launches_per_step": _stage_launches(st, steps),
@@ -973,8 +978,13 @@ def main():
     ap.add_argument("--configs", default="ACDE",
                     help="configurations whose sub-results the default run adds (subset of ACDE, '' for none)")
     ap.add_argument("--c-window", type=int, default=256, help="FP16 workload: channels of the 4096 per step")
+    ap.add_argument("--d-window", type=int, default=1024,
+                    help="calibration workload: channels of the 1024 per step (smaller for profiler captures)")
     ap.add_argument("--e-window", type=int, default=16, help="batched workload: channels per sub-array")
     ap.add_argument("--xengine", default="auto", choices=["auto", "cudacore", "tcgen05"])
+    ap.add_argument("--fengine", default="auto", choices=["auto", "cudacore"],
+                    help="INT8 F-engine: tensor cores where they apply (1024 channels, no delays or filter bank) "
+                         "or the CUDA-core FFT")
     ap.add_argument("--layout", default="planar", choices=["planar", "int8"],
                     help="channelised layout between the engines: planar FP16 codes (TMA X-engine) or complex int8")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
@@ -1004,7 +1014,8 @@ def main():
     if args.workload == "C":
         return _standalone(args, "C", lambda dev, pk: bench_C(args.steps, args.warmup, dev, pk, args.c_window))
     if args.workload == "D":
-        return _standalone(args, "D", lambda dev, pk: bench_D(args.steps, args.warmup, dev, pk, args.comparator))
+        return _standalone(args, "D", lambda dev, pk: bench_D(args.steps, args.warmup, dev, pk, args.comparator,
+                                                              args.d_window))
     if args.workload == "E":
         return _standalone(args, "E", lambda dev, pk: bench_E(args.steps, args.warmup, dev, pk, args.e_window))
     return run_ours(args)
