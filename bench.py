@@ -326,13 +326,19 @@ def run_ours(args):
     d_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
     ms_step, value = job_time_and_rate(ms, cmac_step, args.steps, torch.distributed if ws > 1 else None)
 
-    # ---- end to end through the C ABI with host buffers: pinned raw voltages in, FP64
-    # visibilities out, every step (corr_fx_host pipelines the copies with the engines)
-    vis_pin = torch.empty((N, B), dtype=torch.complex128).pin_memory()
+    # ---- end to end through the C ABI with host buffers: pinned raw voltages in, each
+    # integration's exact visibilities out (INT32 pairs; corr_fx_host_accum pipelines the
+    # copies with the engines and keeps the FP64 long integration on the device)
     e2e_steps = max(1, min(args.steps, 5))
-    if planar:
-        e2e_step = lambda: corr.fx_host(volt_pin, scale, vis_pin)  # noqa: E731
+    accum_out = planar and not fused  # the fused dump keeps no INT32 accumulator
+    if accum_out:
+        out_pin = torch.empty((N, B, 2), dtype=torch.int32).pin_memory()
+        e2e_step = lambda: corr.fx_host_accum(volt_pin, scale, out_pin)  # noqa: E731
     else:
+        out_pin = torch.empty((N, B), dtype=torch.complex128).pin_memory()
+    if planar and not accum_out:
+        e2e_step = lambda: corr.fx_host(volt_pin, scale, out_pin)  # noqa: E731
+    elif not planar:
         vis_dev = torch.empty((N, B), dtype=torch.complex128, device=dev)
 
         def e2e_step():
@@ -340,7 +346,7 @@ def run_ours(args):
             corr.fengine(volt, scale, chan)
             corr.xengine(chan)
             corr.dump(vis_dev)
-            vis_pin.copy_(vis_dev, non_blocking=True)
+            out_pin.copy_(vis_dev, non_blocking=True)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -521,9 +527,13 @@ def run_ours(args):
         "configs": configs,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * cmac_step / (e2e_ms * 1e-3), "unit": "cMAC/s",
-                "h2d_bytes_per_step": int(volt_pin.numel()), "d2h_bytes_per_step": int(vis_pin.numel() * 16),
+                "h2d_bytes_per_step": int(volt_pin.numel()),
+                "d2h_bytes_per_step": int(out_pin.numel() * out_pin.element_size()),
                 "ms_per_step": e2e_ms, "ms_per_step_min": float(min(e2e_blocks)), "ms_per_step_blocks": e2e_blocks,
-                "path": "corr_fx_host (copies pipelined with the engines)" if planar else "copies then kernels"},
+                "path": ("corr_fx_host_accum (copies pipelined with the engines; the integration's INT32 "
+                         "visibilities out, the FP64 long integration kept on the device)" if accum_out
+                         else "corr_fx_host (copies pipelined with the engines; FP64 long integration out)"
+                         if planar else "copies then kernels")},
         "gpu_launches": launches,
         "clocks": clocks,
     }

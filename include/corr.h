@@ -300,6 +300,21 @@ CORR_API corr_status corr_restore_vis(corr_t *h, const double *vis_in, void *str
 CORR_API corr_status corr_fx_host(corr_t *h, const void *volt_host, const float *chan_scale, double *vis_host,
                                   void *stream);
 
+/* The same whole step from host memory (Eqs. 1-2, Section 2), returning this
+ * integration's exact visibilities instead of the long integration:
+ *   acc_host [n_chan][B] complex int32 (2 x int32, Re then Im), host (page-locked
+ *            memory lets the copies run asynchronously): the integration's sums,
+ *            as corr_get_accum would give them; 8 bytes per visibility, half the
+ *            FP64 copy of corr_fx_host.
+ * The integration is also added to the FP64 long-integration buffer on the device
+ * (as corr_dump), which stays there for corr_dump / corr_flush to read. Inputs,
+ * ordering, the first call's allocations and the lifetime rule for volt_host are
+ * those of corr_fx_host. INT8 with CORR_FLAG_PLANAR and without
+ * CORR_FLAG_FUSED_DUMP (which keeps no INT32 accumulator): CORR_EUNSUPPORTED
+ * otherwise; NULL pointers: CORR_EINVAL. */
+CORR_API corr_status corr_fx_host_accum(corr_t *h, const void *volt_host, const float *chan_scale,
+                                        int32_t *acc_host, void *stream);
+
 /* Read and clear the handle's device status word. Returns CORR_ETIMEOUT (or
  * another CORR_* code) if a kernel of this handle gave up early since the last
  * check, CORR_OK otherwise. Synchronises `stream`. */

@@ -66,6 +66,7 @@ SIGNATURES = [
     ("corr_fengine_power_noalloc", _S, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         _P, _P]),
     ("corr_fx_host", _S, [_P, _P, _P, _P, _P]),
+    ("corr_fx_host_accum", _S, [_P, _P, _P, _P, _P]),
     ("corr_set_stage_timing", _S, [_P, ctypes.c_int32]),
     ("corr_stage_times", _S, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     ("corr_batch_create", _S, [ctypes.c_int32, ctypes.POINTER(corr_sub_desc), ctypes.POINTER(corr_opts),

@@ -87,6 +87,11 @@ def corr_fx_host(h, volt_host, chan_scale, vis_host, stream=None) -> None:
           "corr_fx_host")
 
 
+def corr_fx_host_accum(h, volt_host, chan_scale, acc_host, stream=None) -> None:
+    check(_lib.load().corr_fx_host_accum(h, _hptr(volt_host), _ptr(chan_scale), _hptr(acc_host), _stream(stream)),
+          "corr_fx_host_accum")
+
+
 def corr_xengine(h, chan_in, gains=None, stream=None) -> None:
     check(_lib.load().corr_xengine(h, _ptr(chan_in), _ptr(gains), _stream(stream)), "corr_xengine")
 
@@ -185,6 +190,11 @@ class Correlator:
     def fx_host(self, volt_host, chan_scale, vis_host, stream=None):
         """Whole step from host buffers (pipelined copies); see corr_fx_host."""
         corr_fx_host(self.h, volt_host, chan_scale, vis_host, stream)
+
+    def fx_host_accum(self, volt_host, chan_scale, acc_host, stream=None):
+        """Whole step from host buffers, this integration's INT32 visibilities out
+        ([n_chan][B][2] int32 host tensor); see corr_fx_host_accum."""
+        corr_fx_host_accum(self.h, volt_host, chan_scale, acc_host, stream)
 
     def set_pfb(self, window=None):
         """Polyphase filter-bank window [n_taps, n_chan] (float) for the F-engine, or

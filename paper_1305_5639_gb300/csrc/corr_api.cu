@@ -227,6 +227,103 @@ struct corr_s {
     Handle h;
 };
 
+namespace corr {
+
+// corr_fx_host (out = the FP64 long integration) and corr_fx_host_accum (out = this
+// integration's INT32 accumulator, copied while the dump adds it to the FP64 buffer:
+// the dump only reads the accumulator).
+static corr_status fx_host_run(corr_t *c, const void *volt_host, const float *chan_scale, void *out_host,
+                               bool accum_out, void *stream) {
+    if (!c || !volt_host || !chan_scale || !out_host) return CORR_EINVAL;
+    Handle &h = c->h;
+    if (h.precision != CORR_PREC_INT8 || !(h.flags & CORR_FLAG_PLANAR) || !corr::fengine_supported(h.n_chan))
+        return CORR_EUNSUPPORTED;
+    if (accum_out && (h.flags & CORR_FLAG_FUSED_DUMP)) return CORR_EUNSUPPORTED;  // no INT32 accumulator then
+    corr::DeviceGuard dg(h.device);
+    cudaStream_t st = corr::as_stream(stream);
+    {
+        const corr_status s = corr::flush_dump(h, st);  // this pipeline dumps per channel block itself
+        if (s != CORR_OK) return s;
+    }
+    constexpr int NB = 8, NC = 8;  // input blocks (copy-in || F-engine), channel blocks (X + dump || copy-out)
+    const size_t volt_bytes = (size_t)h.n_in * h.n_spectra * h.n_chan * 2;
+    const size_t chan_bytes = (size_t)h.n_chan * 2 * h.n_in * h.n_spectra * 2;
+    if (!h.fx_ready) {
+        // all or nothing: a failed allocation or creation releases whatever this
+        // attempt made, so that a retry starts again from scratch
+        bool ok = cudaMalloc(&h.fx_volt, volt_bytes) == cudaSuccess && cudaMalloc(&h.fx_chan, chan_bytes) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h.fx_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h.fx_out, cudaStreamNonBlocking) == cudaSuccess;
+        for (cudaEvent_t &e : h.fx_ev)
+            ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            corr::free_fx(h);
+            corr::set_error_text("corr_fx_host: allocating the device copies or creating the copy streams failed");
+            return CORR_ENOMEM;
+        }
+        h.fx_ready = true;
+    }
+    // ev[1..NB]: input block b copied; ev[NB+1..NB+NC]: channel block dumped;
+    // ev[NB+NC+1]: all copies out done; ev[NB+NC+2]: the F-engine has read the device
+    // copy of the inputs (recorded by the previous call). The copy-in waits only for
+    // that, not for `stream`, so that it overlaps the previous call's X-engine and
+    // copy-out when calls are issued back to back.
+    cudaEvent_t *ev = h.fx_ev;
+    CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_in, ev[NB + NC + 2], 0));
+    const size_t row = (size_t)h.n_spectra * h.n_chan * 2;  // bytes of one input's time series
+    const int ib = (h.n_in + NB - 1) / NB;
+    for (int b = 0; b < NB; ++b) {
+        const int i0 = b * ib, i1 = std::min(h.n_in, i0 + ib);
+        if (i1 > i0) {
+            CORR_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(h.fx_volt) + row * i0,
+                                          static_cast<const char *>(volt_host) + row * i0, row * (i1 - i0),
+                                          cudaMemcpyHostToDevice, h.fx_in));
+        }
+        CORR_CUDA_TRY(cudaEventRecord(ev[1 + b], h.fx_in));
+        CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + b], 0));
+        if (i1 <= i0) continue;  // fewer inputs than blocks: the last blocks are empty
+        corr_status s = corr::launch_fengine_range(h, h.fx_volt, chan_scale, h.fx_chan, i0, i1 - i0, st);
+        if (s != CORR_OK) return s;
+    }
+    CORR_CUDA_TRY(cudaEventRecord(ev[NB + NC + 2], st));
+    const bool fused = (h.flags & CORR_FLAG_FUSED_DUMP) != 0;
+    const bool store = h.acc_zero;
+    const int cb = (h.n_chan + NC - 1) / NC;
+    for (int k = 0; k < NC; ++k) {
+        const int c0 = k * cb, c1 = std::min(h.n_chan, c0 + cb);
+        corr_status s = corr::launch_xengine_tma_range(h, h.fx_chan, 2, nullptr, nullptr, h.n_spectra, store, c0, c1,
+                                                       st);
+        if (s != CORR_OK) return s;
+        const size_t off = (size_t)c0 * h.n_base;
+        if (accum_out) {
+            // copy the block's INT32 sums out while the dump adds them to the FP64 buffer
+            CORR_CUDA_TRY(cudaEventRecord(ev[1 + NB + k], st));
+            CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_out, ev[1 + NB + k], 0));
+            if (c1 > c0)
+                CORR_CUDA_TRY(cudaMemcpyAsync(static_cast<int2 *>(out_host) + off, static_cast<const int2 *>(h.acc) + off,
+                                              sizeof(int2) * (size_t)(c1 - c0) * h.n_base, cudaMemcpyDeviceToHost,
+                                              h.fx_out));
+            if ((s = corr::launch_dump_range(h, c0, c1, st)) != CORR_OK) return s;
+            continue;
+        }
+        if (!fused && (s = corr::launch_dump_range(h, c0, c1, st)) != CORR_OK) return s;
+        CORR_CUDA_TRY(cudaEventRecord(ev[1 + NB + k], st));
+        CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_out, ev[1 + NB + k], 0));
+        if (c1 > c0)
+            CORR_CUDA_TRY(cudaMemcpyAsync(static_cast<double2 *>(out_host) + off, h.vis64 + off,
+                                          sizeof(double2) * (size_t)(c1 - c0) * h.n_base, cudaMemcpyDeviceToHost,
+                                          h.fx_out));
+    }
+    CORR_CUDA_TRY(cudaEventRecord(ev[1 + NB + NC], h.fx_out));
+    CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + NB + NC], 0));
+    h.acc_zero = true;
+    h.acc_spectra = 0;
+    return CORR_OK;
+}
+
+}  // namespace corr
+
 extern "C" {
 
 const char *corr_status_str(corr_status s) {
@@ -634,80 +731,13 @@ corr_status corr_selftest_bounded_wait(int32_t device, int64_t limit_ns) {
 
 corr_status corr_fx_host(corr_t *c, const void *volt_host, const float *chan_scale, double *vis_host, void *stream) {
     corr::NvtxScope nvtx_("corr_fx_host");
-    if (!c || !volt_host || !chan_scale || !vis_host) return CORR_EINVAL;
-    Handle &h = c->h;
-    if (h.precision != CORR_PREC_INT8 || !(h.flags & CORR_FLAG_PLANAR) || !corr::fengine_supported(h.n_chan))
-        return CORR_EUNSUPPORTED;
-    corr::DeviceGuard dg(h.device);
-    cudaStream_t st = corr::as_stream(stream);
-    {
-        const corr_status s = corr::flush_dump(h, st);  // this pipeline dumps per channel block itself
-        if (s != CORR_OK) return s;
-    }
-    constexpr int NB = 8, NC = 8;  // input blocks (copy-in || F-engine), channel blocks (X + dump || copy-out)
-    const size_t volt_bytes = (size_t)h.n_in * h.n_spectra * h.n_chan * 2;
-    const size_t chan_bytes = (size_t)h.n_chan * 2 * h.n_in * h.n_spectra * 2;
-    if (!h.fx_ready) {
-        // all or nothing: a failed allocation or creation releases whatever this
-        // attempt made, so that a retry starts again from scratch
-        bool ok = cudaMalloc(&h.fx_volt, volt_bytes) == cudaSuccess && cudaMalloc(&h.fx_chan, chan_bytes) == cudaSuccess &&
-                  cudaStreamCreateWithFlags(&h.fx_in, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaStreamCreateWithFlags(&h.fx_out, cudaStreamNonBlocking) == cudaSuccess;
-        for (cudaEvent_t &e : h.fx_ev)
-            ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
-        if (!ok) {
-            cudaGetLastError();
-            corr::free_fx(h);
-            corr::set_error_text("corr_fx_host: allocating the device copies or creating the copy streams failed");
-            return CORR_ENOMEM;
-        }
-        h.fx_ready = true;
-    }
-    // ev[1..NB]: input block b copied; ev[NB+1..NB+NC]: channel block dumped;
-    // ev[NB+NC+1]: all copies out done; ev[NB+NC+2]: the F-engine has read the device
-    // copy of the inputs (recorded by the previous call). The copy-in waits only for
-    // that, not for `stream`, so that it overlaps the previous call's X-engine and
-    // copy-out when calls are issued back to back.
-    cudaEvent_t *ev = h.fx_ev;
-    CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_in, ev[NB + NC + 2], 0));
-    const size_t row = (size_t)h.n_spectra * h.n_chan * 2;  // bytes of one input's time series
-    const int ib = (h.n_in + NB - 1) / NB;
-    for (int b = 0; b < NB; ++b) {
-        const int i0 = b * ib, i1 = std::min(h.n_in, i0 + ib);
-        if (i1 > i0) {
-            CORR_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(h.fx_volt) + row * i0,
-                                          static_cast<const char *>(volt_host) + row * i0, row * (i1 - i0),
-                                          cudaMemcpyHostToDevice, h.fx_in));
-        }
-        CORR_CUDA_TRY(cudaEventRecord(ev[1 + b], h.fx_in));
-        CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + b], 0));
-        if (i1 <= i0) continue;  // fewer inputs than blocks: the last blocks are empty
-        corr_status s = corr::launch_fengine_range(h, h.fx_volt, chan_scale, h.fx_chan, i0, i1 - i0, st);
-        if (s != CORR_OK) return s;
-    }
-    CORR_CUDA_TRY(cudaEventRecord(ev[NB + NC + 2], st));
-    const bool fused = (h.flags & CORR_FLAG_FUSED_DUMP) != 0;
-    const bool store = h.acc_zero;
-    const int cb = (h.n_chan + NC - 1) / NC;
-    for (int k = 0; k < NC; ++k) {
-        const int c0 = k * cb, c1 = std::min(h.n_chan, c0 + cb);
-        corr_status s = corr::launch_xengine_tma_range(h, h.fx_chan, 2, nullptr, nullptr, h.n_spectra, store, c0, c1,
-                                                       st);
-        if (s == CORR_OK && !fused) s = corr::launch_dump_range(h, c0, c1, st);
-        if (s != CORR_OK) return s;
-        CORR_CUDA_TRY(cudaEventRecord(ev[1 + NB + k], st));
-        CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_out, ev[1 + NB + k], 0));
-        if (c1 > c0) {
-            const size_t off = (size_t)c0 * h.n_base;
-            CORR_CUDA_TRY(cudaMemcpyAsync(vis_host + 2 * off, h.vis64 + off, sizeof(double2) * (size_t)(c1 - c0) * h.n_base,
-                                          cudaMemcpyDeviceToHost, h.fx_out));
-        }
-    }
-    CORR_CUDA_TRY(cudaEventRecord(ev[1 + NB + NC], h.fx_out));
-    CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + NB + NC], 0));
-    h.acc_zero = true;
-    h.acc_spectra = 0;
-    return CORR_OK;
+    return corr::fx_host_run(c, volt_host, chan_scale, vis_host, false, stream);
+}
+
+corr_status corr_fx_host_accum(corr_t *c, const void *volt_host, const float *chan_scale, int32_t *acc_host,
+                               void *stream) {
+    corr::NvtxScope nvtx_("corr_fx_host_accum");
+    return corr::fx_host_run(c, volt_host, chan_scale, acc_host, true, stream);
 }
 
 corr_status corr_check_status(corr_t *c, void *stream) {

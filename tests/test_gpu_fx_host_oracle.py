@@ -68,3 +68,58 @@ def test_fx_host_matches_oracle_chain(cuda_ok, n_ant, n_pol, N, K):
     assert n_exact > 0.5  # most visibilities are pinned exactly
     c.check_status()
     c.close()
+
+
+@pytest.mark.parametrize("n_ant,n_pol,N,K", [(4, 2, 64, 64), (6, 2, 1024, 16)])
+def test_fx_host_accum_matches_oracle_chain(cuda_ok, n_ant, n_pol, N, K):
+    """corr_fx_host_accum: each call's INT32 output is that integration alone (oracle
+    chain, same bound for codes near a rounding tie), and the FP64 long integration it
+    keeps on the device is the exact sum of the calls' outputs."""
+    n_in = n_ant * n_pol
+    sigma = 16.0
+    rng = np.random.default_rng(N + K + 1)
+    scale = (rng.uniform(0.8, 1.25, N) * 16.0 / (sigma * np.sqrt(N))).astype(np.float32)
+    c = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
+    acc = torch.zeros((N, c.n_base, 2), dtype=torch.int32).pin_memory()
+    total = np.zeros((N, c.n_base, 2), np.int64)
+    for t in range(2):
+        v = synth.volt_int8(n_ant, n_pol, N, K, seed=500 + 3 * t + N, lo=-128)
+        S = oracle.channelise(v, N)
+        q, margin = oracle.requant(S, scale)
+        eps = 8 * np.log2(N) * 2.0 ** -24 * np.sqrt(np.mean(np.abs(S) ** 2)) * scale.max() * 8
+        unsure = margin <= eps
+        want = oracle.cmac(q)
+        slack = _flip_bound(q, unsure)
+        c.fx_host_accum(torch.from_numpy(v).pin_memory(), torch.from_numpy(scale).to(DEV), acc)
+        torch.cuda.synchronize()
+        got = acc.numpy().astype(np.int64)
+        sure = slack == 0
+        assert sure.mean() > 0.5
+        for comp in range(2):
+            assert np.array_equal(got[..., comp][sure], want[..., comp][sure]), t
+            assert np.all(np.abs(got[..., comp] - want[..., comp]) <= slack), t
+        total += got
+    vis = c.dump().cpu().numpy()  # the FP64 long integration of both calls
+    assert np.array_equal(vis.real, total[..., 0].astype(np.float64))
+    assert np.array_equal(vis.imag, total[..., 1].astype(np.float64))
+    c.check_status()
+    c.close()
+
+
+def test_fx_host_accum_rejections(cuda_ok):
+    """No INT32 accumulator with the fused dump; NULL buffers are rejected."""
+    n_ant, n_pol, N, K = 2, 2, 64, 16
+    v = torch.from_numpy(synth.volt_int8(n_ant, n_pol, N, K, seed=9)).pin_memory()
+    scale = torch.full((N,), 0.125, device=DEV)
+    c = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True, fused_dump=True)
+    acc = torch.zeros((N, c.n_base, 2), dtype=torch.int32).pin_memory()
+    with pytest.raises(api.CorrError) as e:
+        c.fx_host_accum(v, scale, acc)
+    assert e.value.status == api._lib.CORR_EUNSUPPORTED
+    c.close()
+    c = api.Correlator(n_ant, n_pol, N, K, precision="int8", planar=True)
+    st = api._lib.load().corr_fx_host_accum(c.h, None, api._ptr(scale), api._hptr(acc), None)
+    assert st == api._lib.CORR_EINVAL
+    st = api._lib.load().corr_fx_host_accum(c.h, api._hptr(v), api._ptr(scale), None, None)
+    assert st == api._lib.CORR_EINVAL
+    c.close()
