@@ -19,7 +19,7 @@
 // then per block of channels, the operand passes of the next block on a side stream
 // overlapping the GEMM of the current one (two operand buffers):
 //   k_adj_aprep  A_f planes [f][Re_h, Im_h, Re_l, Im_l][m][j]   reads G, writes 8 B / entry
-//   k_adj_bprep  conj(X_f)^T planes [f][4][a][j]           reads X, writes 8 B / sample
+//   k_adj_bprep  X_f^T planes [f][4][a][j]                  reads X, writes 8 B / sample
 //   k_xeng_tma<kAdj>  GEMM + epilogue (dX, dg partials)
 // and one fixed-order reduction of the dg partials over all channels.
 #include <cuda_fp16.h>
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) k_adj_aprep(const float2 *__restrict__ Gp
     }
 }
 
-// conj(X_f)^T as four FP16 planes [f - c0][plane][a][j]: one CTA per 64 inputs j x 64
+// X_f^T as four FP16 planes [f - c0][plane][a][j]: one CTA per 64 inputs j x 64
 // spectra a, read as 16-byte pairs of spectra, transposed through shared memory.
 // n_in and K must be multiples of 8.
 __global__ void __launch_bounds__(256) k_adj_bprep(const float2 *__restrict__ X, __half *__restrict__ Bt, int n_in,
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) k_adj_bprep(const float2 *__restrict__ X,
         for (int q = 0; q < 8; ++q) {
             const float2 x = T[(8 * ch + q) * kPTS + r];
             re[q] = x.x;
-            im[q] = -x.y;
+            im[q] = x.y;
         }
         store8_planes(re, im, Bf + (size_t)a * n_in + jc, plane);
     }

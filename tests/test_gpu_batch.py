@@ -79,3 +79,37 @@ def test_batch_workload_sample_subarrays(cuda_ok):
     for X, v in zip(data, b.vis):
         assert np.array_equal(v.cpu().numpy().astype(np.int64), oracle.cmac(X))
     b.close()
+
+
+def test_batch_workload_full_launch_sampled(cuda_ok, tmp_path):
+    """The batched workload as the bench times it: all 64 seed-0 sub-arrays on a
+    16-channel window each, complex int8 sigma = 16 as planar FP16 codes, one tuned
+    graph-replayed launch. Sampled parity against the oracle on every sub-array (one
+    channel each): the triangle of its first 64 inputs, and 16 random pairs (i >= j)
+    anywhere in it; bit-exact."""
+    W = 16
+    subs = synth.subarrays(seed=0)
+    assert len(subs) == 64
+    gen = torch.Generator(device=DEV).manual_seed(0)
+    planes = []
+    for d in subs:
+        z = torch.randn((W, 2, d["n_in"], d["n_spectra"]), generator=gen, device=DEV) * 16.0
+        planes.append(torch.clamp(torch.round(z), -127, 127).to(torch.float16).contiguous())
+    b = api.Batch(planes)
+    b.tune(tmp_path / "tune.json")
+    b.run()
+    b.run()  # a replay overwrites
+    b.check_status()
+    rng = np.random.default_rng(0)
+    for k, (d, p, v) in enumerate(zip(subs, planes, b.vis)):
+        f, n_in = k % W, d["n_in"]
+        X = np.ascontiguousarray(np.transpose(p[f].cpu().numpy(), (1, 2, 0)).astype(np.int8))[None]  # [1, n_in, K, 2]
+        got = v[f].cpu().numpy().astype(np.int64)
+        m = min(n_in, 64)
+        want = oracle.cmac(X[:, :m])[0]  # the packed triangle of the first m inputs is a prefix
+        assert np.array_equal(got[: m * (m + 1) // 2], want), k
+        for _ in range(16):
+            i, j = sorted(rng.integers(0, n_in, 2))[::-1]
+            pair = oracle.cmac(X[:, [j, i]])[0]  # packed (0,0), (1,0), (1,1): (1,0) is V_ij
+            assert np.array_equal(got[i * (i + 1) // 2 + j], pair[1]), (k, i, j)
+    b.close()
