@@ -692,7 +692,7 @@ def bench_A(steps, warmup, dev, peaks, clocks_mhz):
                     "d_i = i samples",
         "ms_per_step": ms, "cmac_per_s": cm / (ms * 1e-3),
         "stages_ms": _stage_ms(st, steps), "launches_per_step": _stage_launches(st, steps),
-        "roofline": {"kernel": "k_xeng_f32 (FP32 CUDA-core X-engine)", "bound": "alu",
+        "roofline": {"kernel": "k_xeng_f32_small (FP32 CUDA-core X-engine for few inputs: one CTA per channel, one thread per pair)", "bound": "alu",
                      "achieved": 8.0 * cm / (x_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": 8.0 * cm / (x_ms * 1e-3) / 1e12 / fp32_peak,
                      "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop at {clocks_mhz:.0f} MHz"},

@@ -106,6 +106,65 @@ __global__ void __launch_bounds__(NTH) k_xeng_f32(const float2 *__restrict__ X, 
     }
 }
 
+// Few inputs (n_in <= kSmallIn, at most 253 packed pairs): a 64 x 64 tile would leave
+// most of its threads idle, so one CTA takes one channel and each thread one packed
+// pair (i >= j), the channel's spectra staged in shared memory in chunks of kSmallKC
+// as [spectrum][input]. Four partial sums per pair (spectra a = r mod 4) keep four
+// independent FMA chains in flight; they are added in a fixed order at the end, so
+// the result is run-to-run identical.
+constexpr int kSmallIn = 22;
+constexpr int kSmallKC = 64;
+
+__global__ void __launch_bounds__(NTH) k_xeng_f32_small(const float2 *__restrict__ X, float2 *__restrict__ acc,
+                                                        const float2 *__restrict__ gains, int n_in, int K,
+                                                        long long B, int store) {
+    __shared__ float2 sx[kSmallKC][kSmallIn + 1];
+    const int chan = blockIdx.x;
+    const int p = threadIdx.x;
+    int i = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= p) ++i;
+    while (i * (i + 1) / 2 > p) --i;
+    const int j = p - i * (i + 1) / 2;
+    const bool live = p < B;
+    const float2 *Xc = X + (size_t)chan * n_in * K;
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int a0 = 0; a0 < K; a0 += kSmallKC) {
+        for (int e = threadIdx.x; e < n_in * kSmallKC; e += NTH) {
+            const int r = e / kSmallKC, a = e % kSmallKC;
+            sx[a][r] = a0 + a < K ? __ldg(Xc + (size_t)r * K + a0 + a) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (live) {
+#pragma unroll 4
+            for (int a = 0; a < kSmallKC; a += 4) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    // x_i conj(x_j)
+                    const float2 xi = sx[a + r][i], xj = sx[a + r][j];
+                    re[r] = fmaf(xi.x, xj.x, fmaf(xi.y, xj.y, re[r]));
+                    im[r] = fmaf(xi.y, xj.x, fmaf(-xi.x, xj.y, im[r]));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!live) return;
+    float2 v = make_float2((re[0] + re[1]) + (re[2] + re[3]), (im[0] + im[1]) + (im[2] + im[3]));
+    if (gains) {
+        const float2 gi = __ldg(gains + i), gj = __ldg(gains + j);
+        // g_i conj(g_j)
+        const float2 w = make_float2(gi.x * gj.x + gi.y * gj.y, gi.y * gj.x - gi.x * gj.y);
+        v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+    }
+    const size_t b = (size_t)chan * B + p;
+    if (store) {
+        acc[b] = v;
+    } else {
+        const float2 o = acc[b];
+        acc[b] = make_float2(o.x + v.x, o.y + v.y);
+    }
+}
+
 __device__ __forceinline__ uint32_t rot_word(uint32_t w) {
     // bytes [re0 im0 re1 im1] -> [im0 ~re0 im1 ~re1] (~re = -re - 1)
     const uint32_t sw = __byte_perm(w, 0u, 0x2301);  // [im0 re0 im1 re1]
@@ -213,6 +272,10 @@ corr_status launch_xengine_cudacore(const Handle &h, const void *chan_in, const 
     if (h.precision == CORR_PREC_INT8) {
         k_xeng_i8<<<grid, NTH, 0, st>>>(static_cast<const char2 *>(chan_in), static_cast<int2 *>(h.acc), h.n_in,
                                         h.n_spectra, h.n_base, store ? 1 : 0);
+    } else if (h.n_in <= kSmallIn) {
+        k_xeng_f32_small<<<h.n_chan, NTH, 0, st>>>(static_cast<const float2 *>(chan_in),
+                                                   static_cast<float2 *>(h.acc), gains, h.n_in, h.n_spectra,
+                                                   h.n_base, store ? 1 : 0);
     } else {
         k_xeng_f32<<<grid, NTH, 0, st>>>(static_cast<const float2 *>(chan_in), static_cast<float2 *>(h.acc),
                                          gains, h.n_in, h.n_spectra, h.n_base, store ? 1 : 0);

@@ -89,7 +89,9 @@ def test_fengine_power(cuda_ok):
 
 
 # --------------------------------------------------------------------------- X-engine (CUDA cores)
-@pytest.mark.parametrize("n_in,K,n_chan", [(70, 37, 3), (16, 64, 2), (1, 5, 2), (129, 16, 1)])
+# few inputs (<= 22: one CTA per channel, one thread per pair) and the tiled kernel
+@pytest.mark.parametrize("n_in,K,n_chan", [(70, 37, 3), (16, 64, 2), (1, 5, 2), (129, 16, 1), (22, 131, 3),
+                                         (23, 40, 2), (8, 1000, 2)])
 def test_xengine_cudacore_fp32(cuda_ok, n_in, K, n_chan):
     X = synth.chan_sources(n_chan, n_in, K, n_src=2, seed=1, src_amp=0.5)
     c = api.Correlator(n_in, 1, n_chan, K, precision="fp32", xengine="cudacore")
@@ -114,14 +116,31 @@ def test_xengine_cudacore_int8_exact(cuda_ok, n_in, K, n_chan):
     c.close()
 
 
-def test_xengine_gains_fp32(cuda_ok):
-    n_in, K, n_chan = 40, 24, 2
+@pytest.mark.parametrize("n_in", [40, 16])
+def test_xengine_gains_fp32(cuda_ok, n_in):
+    K, n_chan = 24, 2
     X = synth.chan_sources(n_chan, n_in, K, n_src=1, seed=3, src_amp=0.3)
     g = synth.gains(n_in, seed=3)
     c = api.Correlator(n_in, 1, n_chan, K)
     c.xengine(torch.from_numpy(X).to(DEV), torch.from_numpy(g).to(DEV))
     V = c.accum().cpu().numpy().astype(np.complex128)
     ref = oracle.apply_gains(oracle.cmac(X), g, n_in)
+    emax, _ = norm_err(V, ref, n_in)
+    assert emax <= 1e-5
+    c.close()
+
+
+@pytest.mark.parametrize("n_in", [40, 16])
+def test_xengine_fp32_accumulates_two_calls(cuda_ok, n_in):
+    # the second call of an integration adds to the first (both FP32 kernels)
+    K, n_chan = 70, 2
+    X1 = synth.chan_sources(n_chan, n_in, K, n_src=1, seed=4, src_amp=0.3)
+    X2 = synth.chan_sources(n_chan, n_in, K, n_src=1, seed=5, src_amp=0.3)
+    c = api.Correlator(n_in, 1, n_chan, K, precision="fp32", xengine="cudacore")
+    c.xengine(torch.from_numpy(X1).to(DEV))
+    c.xengine(torch.from_numpy(X2).to(DEV))
+    V = c.accum().cpu().numpy().astype(np.complex128)
+    ref = oracle.cmac(np.concatenate([X1, X2], axis=2))
     emax, _ = norm_err(V, ref, n_in)
     assert emax <= 1e-5
     c.close()
