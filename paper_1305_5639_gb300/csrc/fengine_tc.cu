@@ -50,7 +50,6 @@ constexpr int kFtSB = 16;              // spectra per item
 constexpr int kFtRoww = kFtSB / 2;     // staging row: 8 words of 16-bit code pairs
 constexpr int kFtSw = 2;               // staging swizzle shift: log2(32 / kFtRoww)
 constexpr int kFtThreads = 16 * 32;
-constexpr uint32_t kSleepNs = 20000;  // suspend hint of a waiting warp (it wakes on the phase)
 
 constexpr int kTileA = 16384;  // 128 rows x 128 B (64 FP16), 128-byte swizzle
 constexpr int kTileB = 8192;   // 64 rows x 128 B
@@ -176,7 +175,7 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_fengine_tc(const FtParams p) 
     // every lane waits; the warp goes on only if all saw the phase (a timeout in any
     // lane aborts the whole warp, so its control flow stays uniform)
     auto wwait = [&](int b, uint32_t par) {
-        const bool ok = tc::mbar_wait(bar(b), par, abort_flag, p.status, 4000000000ull, true, kSleepNs);
+        const bool ok = tc::mbar_wait(bar(b), par, abort_flag, p.status);
         return __all_sync(0xffffffffu, ok) != 0;
     };
 

@@ -33,21 +33,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// The same test, letting the hardware suspend the thread for up to `hint_ns` while
-// the phase is incomplete (it resumes as soon as the phase completes): a waiting warp
-// then takes no issue slots from the warps that work.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(hint_ns)
-        : "memory");
-    return ok != 0;
-}
-
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -57,14 +42,12 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Bounded wait for the phase of the given parity to complete. Gives up after
 // `limit_ns` (or at once if another role already gave up), records
 // CORR_ETIMEOUT in *status and raises the CTA-wide abort flag.
-// With sleep_ns > 0 each test may suspend the thread for up to that long.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *status,
-                                          uint64_t limit_ns = 4000000000ull, bool respect_abort = true,
-                                          uint32_t sleep_ns = 0) {
+                                          uint64_t limit_ns = 4000000000ull, bool respect_abort = true) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
-        if (sleep_ns ? mbar_try_wait_sleep(bar, parity, sleep_ns) : mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 63u) {
             if (respect_abort && *abort_flag) return false;
             if (global_ns() - t0 > limit_ns) {
