@@ -734,21 +734,46 @@ __global__ void __launch_bounds__((WIDE || (ST && MODE == kInt8)) ? NTHREADS_WID
                     tc::tmem_ld16(d + 128u + 16u * cb, im);
                     tc::tmem_wait_ld();
                     const int a0 = J0 + 64 * h + 16 * cb;
-                    if (i < itm.n_in && a0 + 16 <= p.n_cols) {
-                        // 16 contiguous spectra: 8 x (two complex values in a float4)
-                        const float4 *xr = reinterpret_cast<const float4 *>(p.X + rowoff + a0);
-                        float4 *dr = p.dX ? reinterpret_cast<float4 *>(p.dX + rowoff + a0) : nullptr;
+                    if (a0 + 16 <= p.n_cols) {  // (uniform across the warp)
+                        // 16 contiguous spectra: 8 x (two complex values in a float4). X comes in and
+                        // dX goes out through the warp's 4 KB slice (row r's float4 x at position
+                        // x ^ (r % 8)), so that 8 lanes move each row's 128 contiguous bytes
+                        float4 *sl = reinterpret_cast<float4 *>(sgen + OFF_OSTG + ew * OSTG_WARP);
 #pragma unroll
-                        for (int x = 0; x < 8; ++x) {
-                            const float4 xv = __ldg(xr + x);
-                            const float y0r = __uint_as_float(re[2 * x]) * sc, y0i = __uint_as_float(im[2 * x]) * sc;
-                            const float y1r = __uint_as_float(re[2 * x + 1]) * sc, y1i = __uint_as_float(im[2 * x + 1]) * sc;
-                            pr += xv.x * y0r + xv.y * y0i + xv.z * y1r + xv.w * y1i;
-                            pi += xv.x * y0i - xv.y * y0r + xv.z * y1i - xv.w * y1r;
-                            if (dr)
-                                dr[x] = make_float4(gc.x * y0r - gc.y * y0i, gc.x * y0i + gc.y * y0r,
-                                                    gc.x * y1r - gc.y * y1i, gc.x * y1i + gc.y * y1r);
+                        for (int k = 0; k < 8; ++k) {
+                            const int r = 4 * k + (lane >> 3), c = lane & 7;  // row of the warp, float4 of the row
+                            const int ir = I0 + wq * 32 + r;
+                            sl[r * 8 + (c ^ (r & 7))] =
+                                ir < itm.n_in
+                                    ? __ldg(reinterpret_cast<const float4 *>(p.X + ((size_t)chan * itm.n_in + ir) * p.n_cols + a0) + c)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
+                        __syncwarp();
+                        if (i < itm.n_in) {
+#pragma unroll
+                            for (int x = 0; x < 8; ++x) {
+                                float4 &slot = sl[lane * 8 + (x ^ (lane & 7))];
+                                const float4 xv = slot;
+                                const float y0r = __uint_as_float(re[2 * x]) * sc, y0i = __uint_as_float(im[2 * x]) * sc;
+                                const float y1r = __uint_as_float(re[2 * x + 1]) * sc, y1i = __uint_as_float(im[2 * x + 1]) * sc;
+                                pr += xv.x * y0r + xv.y * y0i + xv.z * y1r + xv.w * y1i;
+                                pi += xv.x * y0i - xv.y * y0r + xv.z * y1i - xv.w * y1r;
+                                slot = make_float4(gc.x * y0r - gc.y * y0i, gc.x * y0i + gc.y * y0r,
+                                                   gc.x * y1r - gc.y * y1i, gc.x * y1i + gc.y * y1r);
+                            }
+                        }
+                        __syncwarp();
+                        if (p.dX) {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const int r = 4 * k + (lane >> 3), c = lane & 7;
+                                const int ir = I0 + wq * 32 + r;
+                                if (ir < itm.n_in)
+                                    reinterpret_cast<float4 *>(p.dX + ((size_t)chan * itm.n_in + ir) * p.n_cols + a0)[c] =
+                                        sl[r * 8 + (c ^ (r & 7))];
+                            }
+                        }
+                        __syncwarp();
                     } else if (i < itm.n_in) {
 #pragma unroll 1
                         for (int x = 0; x < 16; ++x) {
