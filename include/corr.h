@@ -290,12 +290,13 @@ CORR_API corr_status corr_restore_vis(corr_t *h, const double *vis_in, void *str
  *   vis_host   [n_chan][B] complex double, host: receives the FP64 long-integration
  *              buffer after this integration has been added to it (as corr_dump)
  * INT8 with CORR_FLAG_PLANAR only (CORR_EUNSUPPORTED otherwise). The first call
- * allocates device copies of the inputs and of the channelised data. The results
+ * allocates two device copies of the inputs (successive calls fill them in turn)
+ * and one of the channelised data. The results
  * are ordered on `stream`: the call's work is complete when `stream` reaches this
  * point. The copy-in of volt_host is not ordered after earlier work on `stream`: it
- * starts as soon as the previous call's F-engine has consumed the device copy, so
- * that back-to-back calls overlap one integration's copy-in with the previous one's
- * X-engine and copy-out. volt_host must therefore hold the data when the call is
+ * starts as soon as the F-engine of the call before the previous one has consumed
+ * the device copy this call fills, so that back-to-back calls overlap one
+ * integration's copy-in with the previous one's F-engine, X-engine and copy-out. volt_host must therefore hold the data when the call is
  * made and stay unchanged until `stream` reaches this point. */
 CORR_API corr_status corr_fx_host(corr_t *h, const void *volt_host, const float *chan_scale, double *vis_host,
                                   void *stream);

@@ -103,9 +103,11 @@ inline cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
 // Host-buffer pipeline resources (corr_fx_host): device copies, copy streams, events.
 void free_fx(Handle &h) {
-    cudaFree(h.fx_volt);
+    cudaFree(h.fx_volt[0]);
+    cudaFree(h.fx_volt[1]);
     cudaFree(h.fx_chan);
-    h.fx_volt = h.fx_chan = nullptr;
+    h.fx_volt[0] = h.fx_volt[1] = h.fx_chan = nullptr;
+    h.fx_par = 0;
     if (h.fx_in) cudaStreamDestroy(h.fx_in);
     if (h.fx_out) cudaStreamDestroy(h.fx_out);
     h.fx_in = h.fx_out = nullptr;
@@ -251,7 +253,8 @@ static corr_status fx_host_run(corr_t *c, const void *volt_host, const float *ch
     if (!h.fx_ready) {
         // all or nothing: a failed allocation or creation releases whatever this
         // attempt made, so that a retry starts again from scratch
-        bool ok = cudaMalloc(&h.fx_volt, volt_bytes) == cudaSuccess && cudaMalloc(&h.fx_chan, chan_bytes) == cudaSuccess &&
+        bool ok = cudaMalloc(&h.fx_volt[0], volt_bytes) == cudaSuccess &&
+                  cudaMalloc(&h.fx_volt[1], volt_bytes) == cudaSuccess && cudaMalloc(&h.fx_chan, chan_bytes) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h.fx_in, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h.fx_out, cudaStreamNonBlocking) == cudaSuccess;
         for (cudaEvent_t &e : h.fx_ev)
@@ -265,28 +268,31 @@ static corr_status fx_host_run(corr_t *c, const void *volt_host, const float *ch
         h.fx_ready = true;
     }
     // ev[1..NB]: input block b copied; ev[NB+1..NB+NC]: channel block dumped;
-    // ev[NB+NC+1]: all copies out done; ev[NB+NC+2]: the F-engine has read the device
-    // copy of the inputs (recorded by the previous call). The copy-in waits only for
-    // that, not for `stream`, so that it overlaps the previous call's X-engine and
-    // copy-out when calls are issued back to back.
+    // ev[NB+NC+1]: all copies out done; ev[NB+NC+2+p]: the F-engine has read device
+    // copy p of the inputs (recorded by the call before the previous one, which used
+    // the same copy). The copy-in waits only for that, not for `stream`, so that with
+    // calls issued back to back it follows the previous call's copy-in directly,
+    // overlapping that call's F-engine, X-engine and copy-out.
     cudaEvent_t *ev = h.fx_ev;
-    CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_in, ev[NB + NC + 2], 0));
+    const int par = h.fx_par;
+    void *const vdev = h.fx_volt[par];
+    CORR_CUDA_TRY(cudaStreamWaitEvent(h.fx_in, ev[NB + NC + 2 + par], 0));
     const size_t row = (size_t)h.n_spectra * h.n_chan * 2;  // bytes of one input's time series
     const int ib = (h.n_in + NB - 1) / NB;
     for (int b = 0; b < NB; ++b) {
         const int i0 = b * ib, i1 = std::min(h.n_in, i0 + ib);
         if (i1 > i0) {
-            CORR_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(h.fx_volt) + row * i0,
+            CORR_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(vdev) + row * i0,
                                           static_cast<const char *>(volt_host) + row * i0, row * (i1 - i0),
                                           cudaMemcpyHostToDevice, h.fx_in));
         }
         CORR_CUDA_TRY(cudaEventRecord(ev[1 + b], h.fx_in));
         CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + b], 0));
         if (i1 <= i0) continue;  // fewer inputs than blocks: the last blocks are empty
-        corr_status s = corr::launch_fengine_range(h, h.fx_volt, chan_scale, h.fx_chan, i0, i1 - i0, st);
+        corr_status s = corr::launch_fengine_range(h, vdev, chan_scale, h.fx_chan, i0, i1 - i0, st);
         if (s != CORR_OK) return s;
     }
-    CORR_CUDA_TRY(cudaEventRecord(ev[NB + NC + 2], st));
+    CORR_CUDA_TRY(cudaEventRecord(ev[NB + NC + 2 + par], st));
     const bool fused = (h.flags & CORR_FLAG_FUSED_DUMP) != 0;
     const bool store = h.acc_zero;
     const int cb = (h.n_chan + NC - 1) / NC;
@@ -319,6 +325,7 @@ static corr_status fx_host_run(corr_t *c, const void *volt_host, const float *ch
     CORR_CUDA_TRY(cudaStreamWaitEvent(st, ev[1 + NB + NC], 0));
     h.acc_zero = true;
     h.acc_spectra = 0;
+    h.fx_par = par ^ 1;
     return CORR_OK;
 }
 

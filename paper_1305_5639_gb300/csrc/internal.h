@@ -59,9 +59,10 @@ struct Handle {
     float2 *bwd_ws = nullptr;    // corr_backward workspace (dg partials; tensor-core operand planes)
     cudaStream_t bwd_side = nullptr;  // tensor-core backward: side stream for the operand passes
     cudaEvent_t bwd_ev[5] = {};       //   and its events
-    // host-buffer pipeline (corr_fx_host): device copies of the inputs and the
-    // channelised data, two copy streams and per-block events (first use)
-    void *fx_volt = nullptr, *fx_chan = nullptr;
+    // host-buffer pipeline (corr_fx_host): two device copies of the inputs (calls use
+    // them in turn), the channelised data, two copy streams and per-block events (first use)
+    void *fx_volt[2] = {nullptr, nullptr}, *fx_chan = nullptr;
+    int fx_par = 0;  // the input copy the next call fills
     cudaStream_t fx_in = nullptr, fx_out = nullptr;
     cudaEvent_t fx_ev[40] = {};
     bool fx_ready = false;  // every fx_* resource above was created
