@@ -90,6 +90,8 @@ def test_null_handle_calls(lib):
     assert lib.corr_xengine(None, None, None, None) == CORR_EINVAL
     assert lib.corr_dump(None, None, None) == CORR_EINVAL
     assert lib.corr_backward(None, None, None, None, None, None, None) == CORR_EINVAL
+    assert lib.corr_fx_host(None, None, None, None, None) == CORR_EINVAL
+    assert lib.corr_fx_host_accum(None, None, None, None, None) == CORR_EINVAL
     assert lib.corr_n_baselines(None) == -1
     assert lib.corr_set_stage_timing(None, 1) == CORR_EINVAL
     assert lib.corr_stage_times(None, None, None) == CORR_EINVAL
